@@ -1,0 +1,192 @@
+/*
+ * hsvd.h -- C ABI of the GB300 hierarchical merge-and-truncate rank-k SVD.
+ *
+ * The method (Vasudevan & Ramakrishna, arXiv:1710.02812, Section 3 and
+ * Alg. 1): partition each m x n input into a grid of blocks; take a truncated
+ * SVD of every block; merge the blocks' (U, Sigma) along each row slab with
+ * a binary tree of merge-and-truncate (MAT) steps; take V_j, Sigma_j from the
+ * SVD of U_j^T X_j for every slab; merge the (V_j, Sigma_j) with a second
+ * MAT tree; recover U by projection, SVD(X V_r) = U_y S_y V_y^T.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only.  "Device" pointers are CUDA global-memory addresses
+ *    on the device that was current when the plan was made; "host" pointers
+ *    are ordinary (pageable or pinned) host memory.
+ *  - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).
+ *  - Matrices passed in are row-major with a leading dimension in elements
+ *    (lda >= n).  Factors returned are column-major (LAPACK style).
+ *  - Every function returns an hsvd_status; nothing aborts, traps or exits.
+ *    Invalid arguments are rejected with HSVD_EINVAL before any allocation
+ *    or device work.
+ *  - A plan is not thread-safe; one run may be in flight per plan.
+ */
+#ifndef HSVD_H
+#define HSVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSVD_OK = 0,
+  HSVD_EINVAL = 1,       /* invalid argument (nothing was allocated or launched) */
+  HSVD_ENOMEM = 2,       /* device or host allocation failed */
+  HSVD_ECUDA = 3,        /* a CUDA runtime call failed (launch, copy, no device) */
+  HSVD_ENOTREADY = 4,    /* factors requested before any run */
+  HSVD_EUNSUPPORTED = 5  /* valid but not supported by this build (e.g. size) */
+} hsvd_status;
+
+/* Truncation rule applied after every SVD on the path (Section 3: "MAT").
+ * FIXED_K: keep min(k, numerical rank), param = k.
+ * GAMMA:   keep sigma_i >= gamma * sigma_1 of that block / merge, param = gamma in (0,1).
+ * ENERGY:  keep the smallest r with sum_{i<=r} sigma_i^2 >= f * total, param = f in (0,1];
+ *          total = ||B||_F^2 for a block, ||S1||^2 + ||S2||^2 for a merge.
+ * Every rule also drops sigma_i <= rank_tol * sigma_1 and caps at rank_cap. */
+typedef enum {
+  HSVD_TRUNC_FIXED_K = 0,
+  HSVD_TRUNC_GAMMA = 1,
+  HSVD_TRUNC_ENERGY = 2
+} hsvd_trunc;
+
+/* Order of the two MAT trees.  COL_THEN_ROW is the paper's (Alg. 1):
+ * column merges inside each row slab, then row merges of the slabs.
+ * ROW_THEN_COL runs the same algorithm on X^T and swaps U and V. */
+typedef enum {
+  HSVD_TREE_COL_THEN_ROW = 0,
+  HSVD_TREE_ROW_THEN_COL = 1
+} hsvd_tree;
+
+/* Arithmetic of the path.
+ * F64:        FP64 everywhere (input must be F64).
+ * F32:        FP32 GEMMs (SIMT FFMA), FP32 factors and cores.
+ * BF16_MIXED: input converted to / given in BF16; the input-streaming GEMMs
+ *             run on BF16 tensor cores with FP32 accumulation; factors and
+ *             cores in FP32. */
+typedef enum {
+  HSVD_PREC_F64 = 0,
+  HSVD_PREC_F32 = 1,
+  HSVD_PREC_BF16_MIXED = 2
+} hsvd_prec;
+
+typedef enum {
+  HSVD_DTYPE_F64 = 0,
+  HSVD_DTYPE_F32 = 1,
+  HSVD_DTYPE_BF16 = 2
+} hsvd_dtype;
+
+typedef enum {
+  HSVD_WHERE_HOST = 0,
+  HSVD_WHERE_DEVICE = 1
+} hsvd_where;
+
+/* Optional knobs; pass NULL to hsvd_plan for defaults.  Zero / negative
+ * fields mean "default". */
+typedef struct {
+  int32_t oversample;   /* p: block sketch width k' = k + p (default p = k), capped at 256 */
+  int32_t power_iters;  /* q: power steps of the block range finder; 0 = default
+                           (3 for F64, 2 otherwise), -1 = none, > 0 = that many */
+  double rank_tol;      /* relative numerical-zero level (default 1e-12 F64, 1e-5 otherwise) */
+  uint64_t seed;        /* seed of the block sketch matrix (default 0x1710028) */
+  int32_t max_sweeps;   /* one-sided Jacobi sweep cap (default 40) */
+  int32_t host_staging; /* nonzero: reserve device staging for hsvd_run_host */
+} hsvd_options;
+
+/* Device status words, read back by hsvd_status_query. */
+typedef struct {
+  int32_t not_converged;  /* Jacobi cores that hit the sweep cap */
+  int32_t chol_dropped;   /* directions dropped as numerically dependent in CholeskyQR */
+  int32_t nonfinite;      /* cores that saw a NaN / Inf */
+  int32_t min_rank;       /* smallest final rank over the batch */
+  int32_t max_rank;       /* largest final rank over the batch */
+} hsvd_report;
+
+typedef struct hsvd_plan_s* hsvd_plan_t;
+
+/* hsvd_plan -- build the schedule of one batch of independent matrices.
+ *   out         receives the plan (set to NULL on failure).
+ *   batch       number of matrices (>= 1).
+ *   m, n        host arrays[batch] of matrix sizes (each >= 1).
+ *   block_rows, block_cols   block size d x c of Alg. 1 (>= 1); the last
+ *               slab / slice of a matrix may be smaller (ragged).
+ *   mode, param truncation rule (see hsvd_trunc).
+ *   rank_cap    largest rank kept anywhere (1..256); factors are stored with
+ *               this many columns.
+ *   tree        merge order (hsvd_tree).
+ *   prec        arithmetic (hsvd_prec); in_dtype the element type of the
+ *               matrices given to hsvd_run (F64 for PREC_F64, F32 for
+ *               PREC_F32, F32 or BF16 for PREC_BF16_MIXED).
+ *   opts        NULL or knobs.
+ * Allocates all device workspace on the current device.  Errors: EINVAL
+ * (bad argument, nothing allocated), ENOMEM, ECUDA, EUNSUPPORTED. */
+hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const int64_t* n,
+                      int64_t block_rows, int64_t block_cols, hsvd_trunc mode, double param,
+                      int32_t rank_cap, hsvd_tree tree, hsvd_prec prec, hsvd_dtype in_dtype,
+                      const hsvd_options* opts);
+
+/* hsvd_run -- enqueue the whole path on `stream`.
+ *   A, lda      host arrays[batch] of DEVICE pointers to the row-major
+ *               matrices and their leading dimensions (elements).  The
+ *               caller owns them; they must stay valid and unmodified until
+ *               the stream has passed this work.  They are only read.
+ * Asynchronous: returns after enqueueing.  Returns launch errors only
+ * (ECUDA) or EINVAL for a NULL pointer / lda < n. */
+hsvd_status hsvd_run(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream);
+
+/* hsvd_run_host -- as hsvd_run, but A[i] are HOST pointers: the matrices
+ * are copied to plan-owned device staging on `stream` first (the plan must
+ * have been made with opts->host_staging != 0, else EINVAL).  Host memory
+ * must stay valid until the stream has passed the copies. */
+hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream);
+
+/* hsvd_status_query -- read the device status words of the last run.
+ * sync != 0 synchronises the plan's last stream first; with sync == 0 the
+ * values may be stale.  `r` must not be NULL. */
+hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r);
+
+/* hsvd_factors -- results of matrix `idx` of the last run.
+ *   rank   (host int*, may be NULL) receives r, the number of singular triplets.
+ *   U      m x r column-major with leading dimension ldu >= m (may be NULL).
+ *   S      r singular values, descending, non-negative (may be NULL).
+ *   V      n x r column-major with leading dimension ldv >= n (may be NULL).
+ *   where  HSVD_WHERE_HOST: U/S/V are host pointers; the call synchronises
+ *          `stream` and returns with the copies done.
+ *          HSVD_WHERE_DEVICE: device pointers; copies are enqueued on `stream`.
+ * Element type: double for PREC_F64, float otherwise.  Signs are normalised
+ * so the largest-magnitude entry of each U column is positive.  Buffers must
+ * hold rank_cap columns (the rank is only known on the device until sync).
+ * Errors: EINVAL (idx out of range, ld too small), ENOTREADY, ECUDA. */
+hsvd_status hsvd_factors(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* U, int64_t ldu,
+                         void* S, void* V, int64_t ldv, hsvd_where where, void* stream);
+
+/* hsvd_workspace_bytes -- device bytes the plan holds (host query). */
+int64_t hsvd_workspace_bytes(hsvd_plan_t plan);
+
+/* hsvd_launches_per_run -- number of kernel launches one hsvd_run enqueues
+ * (host query; -1 for NULL). */
+int32_t hsvd_launches_per_run(hsvd_plan_t plan);
+
+/* hsvd_destroy -- free everything the plan owns; NULL is accepted. */
+void hsvd_destroy(hsvd_plan_t plan);
+
+/* hsvd_error_string -- static description of a status code. */
+const char* hsvd_error_string(hsvd_status s);
+
+/* hsvd_tree_levels -- host-only: number of MAT levels of a tree over
+ * `count` leaves (ceil(log2 count); Alg. 1 DoMergeOfSlices with the odd
+ * element carried), or -1 for count < 1. */
+int32_t hsvd_tree_levels(int64_t count);
+
+/* hsvd_jacobi_pair -- host-only: the column pair handled by slot `slot` in
+ * round `round` of the round-robin ordering used by the one-sided Jacobi
+ * cores (n even, 0 <= round < n-1, 0 <= slot < n/2).  Returns 0 on success,
+ * EINVAL otherwise.  Exposed so the ordering can be checked without a GPU. */
+hsvd_status hsvd_jacobi_pair(int32_t n, int32_t round, int32_t slot, int32_t* p, int32_t* q);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSVD_H */

@@ -1,0 +1,182 @@
+// Internal types shared by the kernels and the host runtime of libhsvd.
+//
+// Every kernel of the path is *batched*: it takes a device array of task
+// descriptors (one per block / merge / slab / matrix of the current tree
+// level) plus, for the tiled GEMMs, a device array of tile work items, so one
+// launch covers a whole level of Alg. 1 for every matrix of the batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace hsvd {
+
+// Input matrix table, refreshed on the device at every run: the base pointer
+// and leading dimension (elements) of each row-major input.
+struct MatRef {
+  const void* ptr;
+  int64_t ld;
+};
+
+// An extent that is either fixed at plan time or read at run time from a
+// device rank word (ranks chosen by truncation are only known on the device).
+struct Dim {
+  int cap;         // static upper bound
+  const int* dyn;  // nullptr: extent == cap; else extent == min(*dyn, cap)
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int eff(const Dim& d) {
+  if (!d.dyn) return d.cap;
+  int v = *d.dyn;
+  return v < d.cap ? (v < 0 ? 0 : v) : d.cap;
+}
+#endif
+
+// Status words accumulated by the kernels of one run.
+struct DevStatus {
+  int not_converged;
+  int chol_dropped;
+  int nonfinite;
+  int pad;
+};
+
+// ---------------------------------------------------------------- GEMM tasks
+// NN:  C[M x N] = alpha * [A | A2][M x (K + K2)] * B[(K + K2) x N] + beta * C0
+// TN:  C[M x N] = alpha * A^T * B  with A stored K x M, B stored K x N
+// All matrices row-major with leading dimensions in elements.  When
+// mat >= 0, A is the input matrix `mat` of the run table offset by (r0, c0).
+template <class TA, class TB, class TC>
+struct GemmTask {
+  const TA* A;
+  int64_t lda;
+  const TA* A2;  // NN only, nullptr = single segment
+  int64_t lda2;
+  const TB* B;
+  int64_t ldb;
+  TC* C;
+  int64_t ldc;
+  const TC* C0;  // nullptr = no beta term
+  int64_t ldc0;
+  Dim M, N, K, K2;
+  float alpha, beta;
+  int mat;
+  int64_t r0, c0;
+  TC* partial;  // TN split-K: base of this task's partial tiles (nullptr = direct)
+  int kchunk;   // TN split-K: rows of K per chunk (0 = whole K)
+  int nkc;      // number of K chunks
+  int mtiles, ntiles;
+};
+
+// Work item of a tiled GEMM launch: (task, tile row, tile column, K chunk).
+struct GemmItem {
+  int task, mt, nt, kc;
+};
+
+// ---------------------------------------------------------------- small tasks
+// Cholesky of a k x k Gram matrix G with relative pivot dropping, returning
+// the upper factor R (G ~= R^T R) and its inverse (dropped directions have
+// zero rows in R and zero columns in R^{-1}).  If Rprev != nullptr the
+// returned R is R * Rprev (CholeskyQR2 accumulates R = R2 R1).
+template <class T>
+struct CholTask {
+  const T* G;
+  int64_t ldg;
+  Dim k;
+  T* R;  // may be nullptr
+  int64_t ldr;
+  T* Rinv;  // may be nullptr
+  int64_t ldri;
+  const T* Rprev;
+  int64_t ldrp;
+  T* work;  // global scratch (k*k) when the matrix does not fit shared memory
+};
+
+// One-sided Jacobi SVD of a small matrix M (nr x nc): right rotations make
+// the columns of M orthogonal; their norms are the singular values and the
+// normalised columns the left singular vectors.  The rank is chosen by the
+// truncation rule.  load == 0: M[i][j] = src[i*rs + j*cs].  load == 1: M is
+// the merge core E = [[diag(s1), (P + P2) diag(s2)], [0, R diag(s2)]].
+template <class T>
+struct JacobiTask {
+  int load;
+  const T* src;
+  int64_t rs, cs;
+  Dim nr, nc;
+  const T* s1;
+  const T* s2;
+  Dim k1, k2;
+  const T* P;
+  const T* P2;
+  int64_t ldp;
+  const T* R;
+  int64_t ldr;
+  T* U;  // nr x ucap row-major (left vectors, sorted), may be nullptr
+  int64_t ldu;
+  int ucap;
+  T* V;  // nc x nc row-major accumulated rotations (sorted), may be nullptr
+  int64_t ldv;
+  T* sig;        // sorted singular values, ucap entries (zero past the rank)
+  int* rank;     // chosen rank
+  const T* energy;  // total energy for ENERGY (nullptr: from s1,s2 or the core)
+  T* work;       // global scratch when the matrix does not fit shared memory
+};
+
+struct TruncParams {
+  int mode;        // 0 fixed-k, 1 gamma, 2 energy
+  double param;
+  int rank_cap;
+  double rank_tol;
+  int max_sweeps;
+};
+
+// Launchers (defined in gemm.cu / small.cu).
+template <class TA, class TB, class TC>
+cudaError_t launch_gemm_nn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
+                           const MatRef* mats, cudaStream_t s);
+template <class TA, class TB, class TC>
+cudaError_t launch_gemm_tn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
+                           const MatRef* mats, cudaStream_t s);
+template <class TA, class TB, class TC>
+cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
+                               cudaStream_t s);
+template <class T>
+cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
+                        cudaStream_t s);
+template <class T>
+cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                          TruncParams tp, DevStatus* st, cudaStream_t s);
+
+cudaError_t launch_fill_gaussian_f32(float* out, int64_t count, uint64_t seed, cudaStream_t s);
+cudaError_t launch_fill_gaussian_f64(double* out, int64_t count, uint64_t seed, cudaStream_t s);
+cudaError_t launch_f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, int64_t ldd, int64_t rows,
+                               int64_t cols, cudaStream_t s);
+
+// Energy (squared Frobenius norm) of each block: out[t] = ||X_blk||_F^2.
+struct EnergyTask {
+  int mat;
+  int64_t r0, c0;
+  int h, w;
+  void* out;
+};
+template <class TA, class TO>
+cudaError_t launch_block_energy(const EnergyTask* tasks, int ntasks, const MatRef* mats, cudaStream_t s);
+
+// Copy a row-major factor (h x rank, ld) into a column-major destination
+// (ldd), flipping column signs so the largest |entry| of each U column is
+// positive (the same flips applied to the paired V column).
+template <class T>
+cudaError_t launch_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n, const int* rank,
+                                  int kcap, cudaStream_t s);
+template <class T>
+cudaError_t launch_rowmajor_to_colmajor(const T* src, int64_t lds, int rows, const int* rank, int kcap,
+                                        T* dst, int64_t ldd, cudaStream_t s);
+
+// Host-side helpers exported for checks without a GPU.
+int jacobi_pair_host(int n, int r, int s, int* p, int* q);
+bool jacobi_uses_smem(int nrcap, int nccap, bool want_v, size_t elem);
+size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem);
+bool chol_uses_smem(int kcap, size_t elem);
+
+}  // namespace hsvd

@@ -1,0 +1,1210 @@
+// Host runtime and C ABI of libhsvd.
+//
+// hsvd_plan builds, once, the whole schedule of Alg. 1 for a batch of
+// matrices: the grid of blocks (ceil(m/d) x ceil(n/c), ragged last slab and
+// slice), the binary MAT trees (DoMergeOfSlices: adjacent pairs, an odd last
+// element carried), the task tables and tile lists of every batched kernel,
+// and one device arena holding every intermediate factor.  hsvd_run then only
+// refreshes the input pointer table and replays the launch list on a stream;
+// each launch covers one step of one tree level for every block, merge or
+// slab of every matrix of the batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hsvd.h"
+#include "common.cuh"
+
+namespace hsvd {
+
+namespace {
+
+constexpr int TILE = 64;
+constexpr int KCHUNK = 1024;
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+struct Blob {
+  std::vector<char> bytes;
+  size_t dev_off = 0;
+};
+
+struct Step {
+  std::string name;
+  std::function<cudaError_t(cudaStream_t)> run;
+};
+
+struct ProblemOut {
+  int mm = 0, nn = 0;  // dims of the problem view (X or X^T)
+  bool trans = false;  // the view is X^T of the input
+  void* U = nullptr;   // mm x kcap row-major, left vectors of the view
+  void* V = nullptr;   // nn x kcap row-major
+  void* sig = nullptr; // kcap
+  int* rank = nullptr;
+};
+
+}  // namespace
+
+struct PlanImpl {
+  int batch = 0;
+  std::vector<int64_t> m, n;
+  int64_t br = 0, bc = 0;
+  hsvd_trunc mode = HSVD_TRUNC_FIXED_K;
+  double param = 0;
+  int rank_cap = 0;
+  hsvd_tree tree = HSVD_TREE_COL_THEN_ROW;
+  hsvd_prec prec = HSVD_PREC_F32;
+  hsvd_dtype in_dtype = HSVD_DTYPE_F32;
+  int kcap = 0, kp = 0, q = 0, max_sweeps = 40;
+  double rank_tol = 0, tau = 0;
+  uint64_t seed = 0;
+  bool host_staging = false;
+  size_t elem = 4;     // factor element size
+  size_t in_elem = 4;  // input element size as given to hsvd_run
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  char* tables = nullptr;
+  size_t tables_bytes = 0;
+  MatRef* d_mats = nullptr;
+  MatRef* h_mats = nullptr;  // pinned
+  cudaEvent_t mats_done = nullptr;
+  DevStatus* d_status = nullptr;
+  std::vector<void*> conv;     // BF16 copies of FP32 inputs (mixed path)
+  std::vector<void*> staging;  // device copies for hsvd_run_host
+  std::vector<Blob> blobs;
+  std::vector<Step> steps;
+  std::vector<Step> init_steps;
+  std::vector<ProblemOut> outs;
+  bool ran = false;
+  cudaStream_t last_stream = nullptr;
+  int launches_per_run = 0;
+  int dev = 0;
+
+  ~PlanImpl() {
+    if (arena) cudaFree(arena);
+    if (tables) cudaFree(tables);
+    if (d_mats) cudaFree(d_mats);
+    if (d_status) cudaFree(d_status);
+    if (h_mats) cudaFreeHost(h_mats);
+    if (mats_done) cudaEventDestroy(mats_done);
+    for (void* p : conv) cudaFree(p);
+    for (void* p : staging) cudaFree(p);
+  }
+
+  template <class X>
+  const X* table(size_t blob) const {
+    return reinterpret_cast<const X*>(tables + blobs[blob].dev_off);
+  }
+  template <class X>
+  size_t add_blob(const std::vector<X>& v) {
+    Blob b;
+    b.bytes.resize(std::max<size_t>(v.size() * sizeof(X), 16));
+    if (!v.empty()) std::memcpy(b.bytes.data(), v.data(), v.size() * sizeof(X));
+    blobs.push_back(std::move(b));
+    return blobs.size() - 1;
+  }
+};
+
+namespace {
+
+template <class G>
+struct TaOf;
+template <class A, class B, class C>
+struct TaOf<GemmTask<A, B, C>> {
+  using type = A;
+};
+
+inline Dim dimc(int cap) { return Dim{cap, nullptr}; }
+inline Dim dimd(int cap, const int* dyn) { return Dim{cap, dyn}; }
+
+// Runs twice: a sizing pass with base == nullptr (pointers are offsets from
+// zero, never dereferenced) and the real pass over the allocated arena, so
+// both passes produce the same layout.
+template <class T, class TA>
+struct Builder {
+  using GI = GemmTask<TA, T, T>;
+  using GS = GemmTask<T, T, T>;
+  PlanImpl& P;
+  char* base;
+  size_t off = 0;
+
+  Builder(PlanImpl& p, char* b) : P(p), base(b) {}
+
+  template <class X>
+  X* alloc(size_t count) {
+    const size_t bytes = std::max<size_t>(count * sizeof(X), 16);
+    const size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return reinterpret_cast<X*>(reinterpret_cast<uintptr_t>(base) + o);
+  }
+
+  struct Factor {
+    T* U = nullptr;
+    int h = 0;
+    T* sig = nullptr;
+    int* rank = nullptr;
+  };
+
+  Factor new_factor(int h) {
+    Factor f;
+    f.U = alloc<T>((size_t)h * P.kcap);
+    f.h = h;
+    f.sig = alloc<T>(P.kcap);
+    f.rank = alloc<int>(1);
+    return f;
+  }
+
+  TruncParams tparams() const {
+    TruncParams tp;
+    tp.mode = (int)P.mode;
+    tp.param = P.param;
+    tp.rank_cap = P.kcap;
+    tp.rank_tol = P.rank_tol;
+    tp.max_sweeps = P.max_sweeps;
+    return tp;
+  }
+
+  // -------------------------------------------------------------- GEMM steps
+  template <class G>
+  G blank() const {
+    G g;
+    std::memset(&g, 0, sizeof(G));
+    g.alpha = 1.f;
+    g.beta = 0.f;
+    g.mat = -1;
+    return g;
+  }
+
+  // C[M x N] = A[M x K] B  (+ second A segment)  with row-major operands.
+  GS nn(const T* A, int64_t lda, int M, Dim K, const T* B, int64_t ldb, Dim N, T* C, int64_t ldc) {
+    GS g = blank<GS>();
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.C = C;
+    g.ldc = ldc;
+    g.M = dimc(M);
+    g.N = N;
+    g.K = K;
+    g.K2 = dimc(0);
+    return g;
+  }
+  // C[M x N] = A^T B with A stored K x M.
+  GS tn(const T* A, int64_t lda, int K, Dim M, const T* B, int64_t ldb, Dim N, T* C, int64_t ldc) {
+    GS g = blank<GS>();
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.C = C;
+    g.ldc = ldc;
+    g.M = M;
+    g.N = N;
+    g.K = dimc(K);
+    g.K2 = dimc(0);
+    return g;
+  }
+
+  template <class G>
+  void finish_items(std::vector<G>& tasks, bool is_tn, std::vector<GemmItem>& items, std::vector<GemmItem>& red) {
+    for (size_t t = 0; t < tasks.size(); ++t) {
+      G& g = tasks[t];
+      g.mtiles = cdiv(g.M.cap, TILE);
+      g.ntiles = cdiv(g.N.cap, TILE);
+      g.nkc = 1;
+      g.kchunk = 0;
+      g.partial = nullptr;
+      if (g.M.cap <= 0 || g.N.cap <= 0) continue;
+      if (is_tn && g.K.cap > KCHUNK) {
+        g.kchunk = KCHUNK;
+        g.nkc = cdiv(g.K.cap, KCHUNK);
+        g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * TILE * TILE);
+        for (int mt = 0; mt < g.mtiles; ++mt)
+          for (int nt = 0; nt < g.ntiles; ++nt) red.push_back(GemmItem{(int)t, mt, nt, 0});
+      }
+      for (int kc = 0; kc < g.nkc; ++kc)
+        for (int mt = 0; mt < g.mtiles; ++mt)
+          for (int nt = 0; nt < g.ntiles; ++nt) items.push_back(GemmItem{(int)t, mt, nt, kc});
+    }
+  }
+
+  template <class G>
+  void emit_gemm(const std::string& name, std::vector<G> tasks, bool is_tn) {
+    if (tasks.empty()) return;
+    std::vector<GemmItem> items, red;
+    finish_items(tasks, is_tn, items, red);
+    if (items.empty()) return;
+    PlanImpl* p = &P;
+    const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
+    const int ni = (int)items.size();
+    using TAx = typename TaOf<G>::type;
+    if (is_tn) {
+      P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
+                               return launch_gemm_tn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
+                                                                p->d_mats, s);
+                             }});
+      if (!red.empty()) {
+        const size_t br = P.add_blob(red);
+        const int nr = (int)red.size();
+        P.steps.push_back(Step{name + ".reduce", [p, bt, br, nr](cudaStream_t s) {
+                                 return launch_gemm_reduce<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(br), nr, s);
+                               }});
+      }
+    } else {
+      P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
+                               return launch_gemm_nn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
+                                                                p->d_mats, s);
+                             }});
+    }
+  }
+
+  // Product with a block of the input through the problem view:
+  //   C = op(Xv[r0:r0+h, c0:c0+w]) * B,  op = transpose when xt.
+  // When the view is X^T the kernel flips (NN <-> TN) and the block is read
+  // at (c0, r0) of the input.
+  struct InputOp {
+    GI g;
+    bool tn;
+  };
+  InputOp input_op(bool xt, int mat, bool view_t, int64_t r0, int64_t c0, int h, int w, const T* B, int64_t ldb,
+                   Dim N, T* C, int64_t ldc) {
+    InputOp io;
+    GI& g = io.g;
+    g = blank<GI>();
+    g.mat = mat;
+    g.B = B;
+    g.ldb = ldb;
+    g.C = C;
+    g.ldc = ldc;
+    g.N = N;
+    g.K2 = dimc(0);
+    const bool tn = xt != view_t;
+    io.tn = tn;
+    if (!view_t) {
+      g.r0 = r0;
+      g.c0 = c0;
+    } else {
+      g.r0 = c0;
+      g.c0 = r0;
+    }
+    if (!xt && !view_t) {  // NN, A = X block h x w
+      g.M = dimc(h);
+      g.K = dimc(w);
+    } else if (xt && !view_t) {  // TN, A = X block (K = h) x (M = w)
+      g.M = dimc(w);
+      g.K = dimc(h);
+    } else if (!xt && view_t) {  // TN, A = input block w x h (K = w, M = h)
+      g.M = dimc(h);
+      g.K = dimc(w);
+    } else {  // NN, A = input block w x h (M = w, K = h)
+      g.M = dimc(w);
+      g.K = dimc(h);
+    }
+    return io;
+  }
+
+  void emit_input(const std::string& name, std::vector<InputOp>& ops) {
+    if (ops.empty()) return;
+    std::vector<GI> nn_t, tn_t;
+    for (auto& o : ops) (o.tn ? tn_t : nn_t).push_back(o.g);
+    emit_gemm(name, nn_t, false);
+    emit_gemm(name, tn_t, true);
+  }
+
+  // -------------------------------------------------------------- small steps
+  void emit_chol(const std::string& name, std::vector<CholTask<T>> tasks, int kcapl) {
+    if (tasks.empty()) return;
+    if (!chol_uses_smem(kcapl, sizeof(T)))
+      for (auto& t : tasks) t.work = alloc<T>((size_t)kcapl * kcapl);
+    PlanImpl* p = &P;
+    const size_t bt = P.add_blob(tasks);
+    const int nt = (int)tasks.size();
+    const double tau = P.tau;
+    P.steps.push_back(Step{name, [p, bt, nt, kcapl, tau](cudaStream_t s) {
+                             return launch_chol<T>(p->table<CholTask<T>>(bt), nt, kcapl, p->d_status, tau, s);
+                           }});
+  }
+
+  void emit_jacobi(const std::string& name, std::vector<JacobiTask<T>> tasks, int nrcap, int nccap, bool want_v,
+                   TruncParams tp) {
+    if (tasks.empty()) return;
+    if (!jacobi_uses_smem(nrcap, nccap, want_v, sizeof(T))) {
+      const size_t el = jacobi_work_bytes(nrcap, nccap, want_v, sizeof(T)) / sizeof(T);
+      for (auto& t : tasks) t.work = alloc<T>(el);
+    }
+    PlanImpl* p = &P;
+    const size_t bt = P.add_blob(tasks);
+    const int nt = (int)tasks.size();
+    P.steps.push_back(Step{name, [p, bt, nt, nrcap, nccap, want_v, tp](cudaStream_t s) {
+                             return launch_jacobi<T>(p->table<JacobiTask<T>>(bt), nt, nrcap, nccap, want_v, tp,
+                                                     p->d_status, s);
+                           }});
+  }
+
+  JacobiTask<T> jblank() const {
+    JacobiTask<T> j;
+    std::memset(&j, 0, sizeof(j));
+    return j;
+  }
+
+  // CholeskyQR with `passes` passes over A (h x k, row-major, ld lda):
+  // Q = A R^{-1} (orthonormal columns; dropped directions give zero columns)
+  // and, if R is wanted, the accumulated R (k x k, ld kl).
+  struct OrthW {
+    const T* A;
+    int64_t lda;
+    int h;
+    Dim k;
+    int kl;     // static cap of k and leading dim of the small matrices
+    T* tmp;     // h x kl, pass-1 output (passes == 2)
+    T* Q;       // h x kl or nullptr
+    T* R;       // kl x kl or nullptr
+    T* G;
+    T* R1;
+    T* Rinv;
+  };
+
+  OrthW orth_bufs(const T* A, int64_t lda, int h, Dim k, int kl, bool tmp, T* Q, T* R) {
+    OrthW o;
+    o.A = A;
+    o.lda = lda;
+    o.h = h;
+    o.k = k;
+    o.kl = kl;
+    o.tmp = tmp ? alloc<T>((size_t)h * kl) : nullptr;
+    o.Q = Q;
+    o.R = R;
+    o.G = alloc<T>((size_t)kl * kl);
+    o.R1 = R ? alloc<T>((size_t)kl * kl) : nullptr;
+    o.Rinv = alloc<T>((size_t)kl * kl);
+    return o;
+  }
+
+  void emit_orth(const std::string& name, const std::vector<OrthW>& ws, int passes, int kcapl) {
+    if (ws.empty()) return;
+    for (int pass = 0; pass < passes; ++pass) {
+      const bool last = pass == passes - 1;
+      std::vector<GS> gram, mult;
+      std::vector<CholTask<T>> ch;
+      for (const auto& w : ws) {
+        const T* in = pass == 0 ? w.A : w.tmp;
+        const int64_t ldin = pass == 0 ? w.lda : w.kl;
+        gram.push_back(tn(in, ldin, w.h, w.k, in, ldin, w.k, w.G, w.kl));
+        CholTask<T> c;
+        std::memset(&c, 0, sizeof(c));
+        c.G = w.G;
+        c.ldg = w.kl;
+        c.k = w.k;
+        c.Rinv = w.Rinv;
+        c.ldri = w.kl;
+        if (w.R) {
+          if (passes == 1) {
+            c.R = w.R;
+          } else if (pass == 0) {
+            c.R = w.R1;
+          } else {
+            c.R = w.R;
+            c.Rprev = w.R1;
+            c.ldrp = w.kl;
+          }
+          c.ldr = w.kl;
+        }
+        ch.push_back(c);
+        T* out = last ? w.Q : w.tmp;
+        if (out) mult.push_back(nn(in, ldin, w.h, w.k, w.Rinv, w.kl, w.k, out, w.kl));
+      }
+      const std::string tag = name + ".p" + std::to_string(pass + 1);
+      emit_gemm(tag + ".gram", gram, true);
+      emit_chol(tag + ".chol", ch, kcapl);
+      emit_gemm(tag + ".mul", mult, false);
+    }
+  }
+
+  // -------------------------------------------------------------- the path
+  struct BlockW {
+    int mat;
+    bool vt;
+    int64_t r0, c0;
+    int h, w, kpb;
+    T *Y, *Q, *Wm, *W1, *UM, *energy;
+    OrthW oY, oW, oR;
+    Factor out;
+  };
+  struct MergeW {
+    Factor f1, f2, out;
+    int h;
+    T *P, *P2, *Qa, *Qb, *Uo, *UE;
+    OrthW oQ;
+  };
+
+  std::vector<MergeW> make_merges(const std::vector<std::pair<Factor, Factor>>& pairs,
+                                  std::vector<Factor>& outs) {
+    const int kc = P.kcap;
+    std::vector<MergeW> ms;
+    for (auto& pr : pairs) {
+      MergeW mw;
+      mw.f1 = pr.first;
+      mw.f2 = pr.second;
+      mw.h = pr.first.h;
+      mw.out = new_factor(mw.h);
+      mw.P = alloc<T>((size_t)kc * kc);
+      mw.P2 = alloc<T>((size_t)kc * kc);
+      mw.Qa = alloc<T>((size_t)mw.h * kc);
+      mw.Qb = alloc<T>((size_t)mw.h * kc);
+      mw.Uo = alloc<T>((size_t)mw.h * kc);
+      mw.UE = alloc<T>((size_t)2 * kc * kc);
+      T* Rt = alloc<T>((size_t)kc * kc);
+      mw.oQ = orth_bufs(mw.Qb, kc, mw.h, dimd(kc, mw.f2.rank), kc, true, mw.Uo, Rt);
+      ms.push_back(mw);
+      outs.push_back(mw.out);
+    }
+    return ms;
+  }
+
+  // One level of merges (Section 3, Eqs. orthmerge1 / orthmerge):
+  // P = U1^T U2; Q = U2 - U1 P, re-projected once (CGS2); Q = U_o R;
+  // E = [[S1, (P + P2) S2], [0, R S2]]; E = U_E S_E V_E^T, truncated;
+  // U = [U1 U_o] U_E[:, :r].
+  void emit_merge_level(const std::string& name, const std::vector<MergeW>& ms) {
+    if (ms.empty()) return;
+    const int kc = P.kcap;
+    std::vector<GS> g1, g2, g3, g4, g5;
+    std::vector<OrthW> ow;
+    std::vector<JacobiTask<T>> jt;
+    for (const auto& mw : ms) {
+      const Dim k1 = dimd(kc, mw.f1.rank), k2 = dimd(kc, mw.f2.rank);
+      g1.push_back(tn(mw.f1.U, kc, mw.h, k1, mw.f2.U, kc, k2, mw.P, kc));
+      GS a = nn(mw.f1.U, kc, mw.h, k1, mw.P, kc, k2, mw.Qa, kc);
+      a.C0 = mw.f2.U;
+      a.ldc0 = kc;
+      a.alpha = -1.f;
+      a.beta = 1.f;
+      g2.push_back(a);
+      g3.push_back(tn(mw.f1.U, kc, mw.h, k1, mw.Qa, kc, k2, mw.P2, kc));
+      GS b = nn(mw.f1.U, kc, mw.h, k1, mw.P2, kc, k2, mw.Qb, kc);
+      b.C0 = mw.Qa;
+      b.ldc0 = kc;
+      b.alpha = -1.f;
+      b.beta = 1.f;
+      g4.push_back(b);
+      ow.push_back(mw.oQ);
+      JacobiTask<T> j = jblank();
+      j.load = 1;
+      j.s1 = mw.f1.sig;
+      j.s2 = mw.f2.sig;
+      j.k1 = k1;
+      j.k2 = k2;
+      j.P = mw.P;
+      j.P2 = mw.P2;
+      j.ldp = kc;
+      j.R = mw.oQ.R;
+      j.ldr = kc;
+      j.U = mw.UE;
+      j.ldu = kc;
+      j.ucap = kc;
+      j.sig = mw.out.sig;
+      j.rank = mw.out.rank;
+      jt.push_back(j);
+      GS u = nn(mw.f1.U, kc, mw.h, k1, mw.UE, kc, dimd(kc, mw.out.rank), mw.out.U, kc);
+      u.A2 = mw.Uo;
+      u.lda2 = kc;
+      u.K2 = k2;
+      g5.push_back(u);
+    }
+    emit_gemm(name + ".P", g1, true);
+    emit_gemm(name + ".Q", g2, false);
+    emit_gemm(name + ".P2", g3, true);
+    emit_gemm(name + ".Q2", g4, false);
+    emit_orth(name + ".orthQ", ow, 2, kc);
+    emit_jacobi(name + ".core", jt, 2 * kc, 2 * kc, false, tparams());
+    emit_gemm(name + ".U", g5, false);
+  }
+
+  // Binary MAT tree over each list (Alg. 1, DoMergeOfSlices), all lists and
+  // all pairs of one level in one batch.
+  std::vector<Factor> tree(const std::string& name, std::vector<std::vector<Factor>> lists) {
+    int level = 0;
+    for (;;) {
+      std::vector<std::pair<Factor, Factor>> pairs;
+      std::vector<std::pair<size_t, size_t>> where;  // (list, position in next)
+      std::vector<std::vector<Factor>> next(lists.size());
+      bool any = false;
+      for (size_t li = 0; li < lists.size(); ++li) {
+        auto& L = lists[li];
+        if (L.size() > 1) any = true;
+        for (size_t i = 0; i + 1 < L.size(); i += 2) {
+          pairs.push_back({L[i], L[i + 1]});
+          where.push_back({li, next[li].size()});
+          next[li].push_back(Factor());
+        }
+        if (L.size() % 2) next[li].push_back(L.back());
+      }
+      if (!any) break;
+      std::vector<Factor> outs;
+      auto ms = make_merges(pairs, outs);
+      for (size_t i = 0; i < where.size(); ++i) next[where[i].first][where[i].second] = outs[i];
+      emit_merge_level(name + ".L" + std::to_string(level), ms);
+      lists.swap(next);
+      ++level;
+    }
+    std::vector<Factor> roots;
+    for (auto& L : lists) roots.push_back(L.front());
+    return roots;
+  }
+
+  void build() {
+    const int kc = P.kcap, kp = P.kp;
+    const bool vt = P.tree == HSVD_TREE_ROW_THEN_COL;
+    const int64_t brr = vt ? P.bc : P.br;
+    const int64_t bcc = vt ? P.br : P.bc;
+    const TruncParams tp = tparams();
+    P.outs.assign(P.batch, ProblemOut());
+
+    // sketch matrix Omega: (block cols) x kp, shared by every block
+    const int wmax = (int)std::min<int64_t>(bcc, [&] {
+      int64_t mx = 1;
+      for (int b = 0; b < P.batch; ++b) mx = std::max(mx, vt ? P.m[b] : P.n[b]);
+      return mx;
+    }());
+    T* omega = alloc<T>((size_t)wmax * kp);
+    {
+      const int64_t cnt = (int64_t)wmax * kp;
+      const uint64_t seed = P.seed;
+      P.init_steps.push_back(Step{"omega", [omega, cnt, seed](cudaStream_t s) {
+                                    if (sizeof(T) == 8)
+                                      return launch_fill_gaussian_f64(reinterpret_cast<double*>(omega), cnt, seed, s);
+                                    return launch_fill_gaussian_f32(reinterpret_cast<float*>(omega), cnt, seed, s);
+                                  }});
+    }
+
+    // ---------------------------------------------------- level 0: blocks
+    std::vector<BlockW> bw;
+    std::vector<std::vector<std::vector<Factor>>> slab_leaves(P.batch);
+    for (int b = 0; b < P.batch; ++b) {
+      const int64_t mm = vt ? P.n[b] : P.m[b];
+      const int64_t nn = vt ? P.m[b] : P.n[b];
+      const int R = cdiv(mm, brr), C = cdiv(nn, bcc);
+      slab_leaves[b].resize(R);
+      for (int j = 0; j < R; ++j)
+        for (int c = 0; c < C; ++c) {
+          BlockW w;
+          w.mat = b;
+          w.vt = vt;
+          w.r0 = (int64_t)j * brr;
+          w.c0 = (int64_t)c * bcc;
+          w.h = (int)std::min<int64_t>(brr, mm - w.r0);
+          w.w = (int)std::min<int64_t>(bcc, nn - w.c0);
+          w.kpb = std::min(kp, std::min(w.h, w.w));
+          const int k = w.kpb;
+          w.Y = alloc<T>((size_t)w.h * k);
+          w.Q = alloc<T>((size_t)w.h * k);
+          w.Wm = alloc<T>((size_t)w.w * k);
+          w.W1 = alloc<T>((size_t)w.w * k);
+          const int ucap = std::min(kc, k);
+          w.UM = alloc<T>((size_t)k * ucap);
+          w.energy = P.mode == HSVD_TRUNC_ENERGY ? alloc<T>(1) : nullptr;
+          w.oY = orth_bufs(w.Y, k, w.h, dimc(k), k, true, w.Q, nullptr);
+          w.oW = orth_bufs(w.Wm, k, w.w, dimc(k), k, false, w.W1, nullptr);
+          T* Rt = alloc<T>((size_t)k * k);
+          w.oR = orth_bufs(w.Wm, k, w.w, dimc(k), k, true, nullptr, Rt);
+          w.out = new_factor(w.h);
+          bw.push_back(w);
+          slab_leaves[b][j].push_back(w.out);
+        }
+    }
+    if (P.mode == HSVD_TRUNC_ENERGY) {
+      std::vector<EnergyTask> et;
+      for (auto& w : bw) {
+        EnergyTask e;
+        e.mat = w.mat;
+        e.r0 = w.vt ? w.c0 : w.r0;
+        e.c0 = w.vt ? w.r0 : w.c0;
+        e.h = w.vt ? w.w : w.h;
+        e.w = w.vt ? w.h : w.w;
+        e.out = w.energy;
+        et.push_back(e);
+      }
+      PlanImpl* p = &P;
+      const size_t bt = P.add_blob(et);
+      const int nt = (int)et.size();
+      P.steps.push_back(Step{"block.energy", [p, bt, nt](cudaStream_t s) {
+                               return launch_block_energy<TA, T>(p->table<EnergyTask>(bt), nt, p->d_mats, s);
+                             }});
+    }
+    {
+      std::vector<InputOp> ops;
+      for (auto& w : bw)
+        ops.push_back(input_op(false, w.mat, w.vt, w.r0, w.c0, w.h, w.w, omega, kp, dimc(w.kpb), w.Y, w.kpb));
+      emit_input("block.sketch", ops);
+    }
+    auto orth_list = [&](int which) {
+      std::vector<OrthW> v;
+      for (auto& w : bw) v.push_back(which == 0 ? w.oY : (which == 1 ? w.oW : w.oR));
+      return v;
+    };
+    emit_orth("block.orthY", orth_list(0), 2, kp);
+    for (int it = 0; it < P.q; ++it) {
+      std::vector<InputOp> ops;
+      for (auto& w : bw)
+        ops.push_back(input_op(true, w.mat, w.vt, w.r0, w.c0, w.h, w.w, w.Q, w.kpb, dimc(w.kpb), w.Wm, w.kpb));
+      emit_input("block.power" + std::to_string(it) + ".W", ops);
+      emit_orth("block.power" + std::to_string(it) + ".orthW", orth_list(1), 1, kp);
+      ops.clear();
+      for (auto& w : bw)
+        ops.push_back(input_op(false, w.mat, w.vt, w.r0, w.c0, w.h, w.w, w.W1, w.kpb, dimc(w.kpb), w.Y, w.kpb));
+      emit_input("block.power" + std::to_string(it) + ".Y", ops);
+      emit_orth("block.power" + std::to_string(it) + ".orthY", orth_list(0), 2, kp);
+    }
+    {
+      std::vector<InputOp> ops;
+      for (auto& w : bw)
+        ops.push_back(input_op(true, w.mat, w.vt, w.r0, w.c0, w.h, w.w, w.Q, w.kpb, dimc(w.kpb), w.Wm, w.kpb));
+      emit_input("block.project", ops);
+      emit_orth("block.orthR", orth_list(2), 2, kp);
+      std::vector<JacobiTask<T>> jt;
+      std::vector<GS> ut;
+      for (auto& w : bw) {
+        const int ucap = std::min(kc, w.kpb);
+        JacobiTask<T> j = jblank();
+        j.load = 0;
+        j.src = w.oR.R;  // M = R^T: M[i][j] = R[j][i]
+        j.rs = 1;
+        j.cs = w.kpb;
+        j.nr = dimc(w.kpb);
+        j.nc = dimc(w.kpb);
+        j.U = w.UM;
+        j.ldu = ucap;
+        j.ucap = ucap;
+        j.sig = w.out.sig;
+        j.rank = w.out.rank;
+        j.energy = w.energy;
+        jt.push_back(j);
+        ut.push_back(nn(w.Q, w.kpb, w.h, dimc(w.kpb), w.UM, ucap, dimd(ucap, w.out.rank), w.out.U, kc));
+      }
+      emit_jacobi("block.core", jt, kp, kp, false, tp);
+      emit_gemm("block.U", ut, false);
+    }
+
+    // ---------------------------------------------------- column MAT trees
+    std::vector<std::vector<Factor>> lists;
+    std::vector<std::pair<int, int>> owner;  // (matrix, slab)
+    for (int b = 0; b < P.batch; ++b)
+      for (size_t j = 0; j < slab_leaves[b].size(); ++j) {
+        lists.push_back(slab_leaves[b][j]);
+        owner.push_back({b, (int)j});
+      }
+    std::vector<Factor> slabU = tree("colmerge", lists);
+
+    // ---------------------------------------------------- slab step
+    // V_j, Sigma_j = SVD(U_j^T X_j): Z_j^T = X_j^T U_j = Q_z R_z,
+    // R_z = A S C^T  =>  V_j = Q_z A.
+    std::vector<std::vector<Factor>> row_lists(P.batch);
+    {
+      std::vector<InputOp> ops;
+      std::vector<OrthW> ow;
+      std::vector<JacobiTask<T>> jt;
+      std::vector<GS> vt_gemm;
+      for (size_t i = 0; i < slabU.size(); ++i) {
+        const int b = owner[i].first, j = owner[i].second;
+        const int64_t mm = vt ? P.n[b] : P.m[b];
+        const int nn = (int)(vt ? P.m[b] : P.n[b]);
+        const int64_t r0 = (int64_t)j * brr;
+        const int h = (int)std::min<int64_t>(brr, mm - r0);
+        const Factor& Uj = slabU[i];
+        T* Zt = alloc<T>((size_t)nn * kc);
+        T* Qz = alloc<T>((size_t)nn * kc);
+        T* Rt = alloc<T>((size_t)kc * kc);
+        T* UR = alloc<T>((size_t)kc * kc);
+        Factor out = new_factor(nn);
+        const Dim kj = dimd(kc, Uj.rank);
+        ops.push_back(input_op(true, b, vt, r0, 0, h, nn, Uj.U, kc, kj, Zt, kc));
+        ow.push_back(orth_bufs(Zt, kc, nn, kj, kc, true, Qz, Rt));
+        JacobiTask<T> jj = jblank();
+        jj.load = 0;
+        jj.src = Rt;
+        jj.rs = kc;
+        jj.cs = 1;
+        jj.nr = kj;
+        jj.nc = kj;
+        jj.U = UR;
+        jj.ldu = kc;
+        jj.ucap = kc;
+        jj.sig = out.sig;
+        jj.rank = out.rank;
+        jt.push_back(jj);
+        vt_gemm.push_back(nn_(Qz, kc, nn, kj, UR, kc, dimd(kc, out.rank), out.U, kc));
+        row_lists[b].push_back(out);
+      }
+      emit_input("slab.project", ops);
+      emit_orth("slab.orth", ow, 2, kc);
+      emit_jacobi("slab.core", jt, kc, kc, false, tp);
+      emit_gemm("slab.V", vt_gemm, false);
+    }
+
+    // ---------------------------------------------------- row MAT trees
+    std::vector<Factor> vhat = tree("rowmerge", row_lists);
+
+    // ---------------------------------------------------- left-vector recovery
+    // Y = X V_r = Q_y R_y, R_y = A S W^T  =>  U = Q_y A, V = V_r W.
+    {
+      std::vector<InputOp> ops;
+      std::vector<OrthW> ow;
+      std::vector<JacobiTask<T>> jt;
+      std::vector<GS> ug, vg;
+      TruncParams tpf = tp;
+      tpf.mode = 0;
+      tpf.param = kc;
+      for (int b = 0; b < P.batch; ++b) {
+        const int mm = (int)(vt ? P.n[b] : P.m[b]);
+        const int nn = (int)(vt ? P.m[b] : P.n[b]);
+        const Factor& V = vhat[b];
+        const Dim kv = dimd(kc, V.rank);
+        T* Y = alloc<T>((size_t)mm * kc);
+        T* Qy = alloc<T>((size_t)mm * kc);
+        T* Rt = alloc<T>((size_t)kc * kc);
+        T* UR = alloc<T>((size_t)kc * kc);
+        T* WR = alloc<T>((size_t)kc * kc);
+        ProblemOut& po = P.outs[b];
+        po.mm = mm;
+        po.nn = nn;
+        po.trans = vt;
+        T* Uf = alloc<T>((size_t)mm * kc);
+        T* Vf = alloc<T>((size_t)nn * kc);
+        T* sf = alloc<T>(kc);
+        int* rf = alloc<int>(1);
+        po.U = Uf;
+        po.V = Vf;
+        po.sig = sf;
+        po.rank = rf;
+        ops.push_back(input_op(false, b, vt, 0, 0, mm, nn, V.U, kc, kv, Y, kc));
+        ow.push_back(orth_bufs(Y, kc, mm, kv, kc, true, Qy, Rt));
+        JacobiTask<T> jj = jblank();
+        jj.load = 0;
+        jj.src = Rt;
+        jj.rs = kc;
+        jj.cs = 1;
+        jj.nr = kv;
+        jj.nc = kv;
+        jj.U = UR;
+        jj.ldu = kc;
+        jj.ucap = kc;
+        jj.V = WR;
+        jj.ldv = kc;
+        jj.sig = sf;
+        jj.rank = rf;
+        jt.push_back(jj);
+        ug.push_back(nn_(Qy, kc, mm, kv, UR, kc, dimd(kc, rf), Uf, kc));
+        vg.push_back(nn_(V.U, kc, nn, kv, WR, kc, dimd(kc, rf), Vf, kc));
+      }
+      emit_input("final.project", ops);
+      emit_orth("final.orth", ow, 2, kc);
+      emit_jacobi("final.core", jt, kc, kc, true, tpf);
+      emit_gemm("final.U", ug, false);
+      emit_gemm("final.V", vg, false);
+      for (int b = 0; b < P.batch; ++b) {
+        ProblemOut po = P.outs[b];
+        T* su = static_cast<T*>(po.trans ? po.V : po.U);
+        T* sv = static_cast<T*>(po.trans ? po.U : po.V);
+        const int mu = po.trans ? po.nn : po.mm;
+        const int mv = po.trans ? po.mm : po.nn;
+        const int* rk = po.rank;
+        P.steps.push_back(Step{"final.signs", [su, sv, mu, mv, rk, kc](cudaStream_t s) {
+                                 return launch_sign_normalise<T>(su, kc, mu, sv, kc, mv, rk, kc, s);
+                               }});
+      }
+    }
+  }
+
+  GS nn_(const T* A, int64_t lda, int M, Dim K, const T* B, int64_t ldb, Dim N, T* C, int64_t ldc) {
+    return nn(A, lda, M, K, B, ldb, N, C, ldc);
+  }
+};
+
+template <class T, class TA>
+hsvd_status build_plan(PlanImpl& P) {
+  {
+    Builder<T, TA> sizing(P, nullptr);
+    sizing.build();
+    P.arena_bytes = sizing.off;
+  }
+  P.steps.clear();
+  P.init_steps.clear();
+  P.blobs.clear();
+  P.outs.clear();
+  if (cudaMalloc(&P.arena, std::max<size_t>(P.arena_bytes, 256)) != cudaSuccess) {
+    P.arena = nullptr;
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  Builder<T, TA> real(P, P.arena);
+  real.build();
+  if (real.off != P.arena_bytes) return HSVD_ECUDA;  // layout must be identical
+  size_t total = 0;
+  for (auto& b : P.blobs) {
+    b.dev_off = total;
+    total = (total + b.bytes.size() + 255) & ~size_t(255);
+  }
+  P.tables_bytes = std::max<size_t>(total, 256);
+  if (cudaMalloc(&P.tables, P.tables_bytes) != cudaSuccess) {
+    P.tables = nullptr;
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  std::vector<char> host(P.tables_bytes, 0);
+  for (auto& b : P.blobs) std::memcpy(host.data() + b.dev_off, b.bytes.data(), b.bytes.size());
+  if (cudaMemcpy(P.tables, host.data(), P.tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return HSVD_ECUDA;
+  for (auto& st : P.init_steps)
+    if (st.run(nullptr) != cudaSuccess) return HSVD_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return HSVD_ECUDA;
+  P.launches_per_run = (int)P.steps.size();
+  return HSVD_OK;
+}
+
+bool valid_dims(int32_t batch, const int64_t* m, const int64_t* n) {
+  if (batch < 1 || !m || !n) return false;
+  for (int i = 0; i < batch; ++i)
+    if (m[i] < 1 || n[i] < 1 || m[i] > (int64_t(1) << 30) || n[i] > (int64_t(1) << 30)) return false;
+  return true;
+}
+
+}  // namespace
+}  // namespace hsvd
+
+using hsvd::PlanImpl;
+
+struct hsvd_plan_s {
+  PlanImpl impl;
+};
+
+extern "C" {
+
+const char* hsvd_error_string(hsvd_status s) {
+  switch (s) {
+    case HSVD_OK: return "success";
+    case HSVD_EINVAL: return "invalid argument";
+    case HSVD_ENOMEM: return "out of memory";
+    case HSVD_ECUDA: return "CUDA runtime error";
+    case HSVD_ENOTREADY: return "no run has completed on this plan";
+    case HSVD_EUNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+int32_t hsvd_tree_levels(int64_t count) {
+  if (count < 1) return -1;
+  int32_t lv = 0;
+  while (count > 1) {
+    count = (count + 1) / 2;
+    ++lv;
+  }
+  return lv;
+}
+
+hsvd_status hsvd_jacobi_pair(int32_t n, int32_t round, int32_t slot, int32_t* p, int32_t* q) {
+  if (!p || !q) return HSVD_EINVAL;
+  int pp, qq;
+  if (hsvd::jacobi_pair_host(n, round, slot, &pp, &qq)) return HSVD_EINVAL;
+  *p = pp;
+  *q = qq;
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const int64_t* n, int64_t block_rows,
+                      int64_t block_cols, hsvd_trunc mode, double param, int32_t rank_cap, hsvd_tree tree,
+                      hsvd_prec prec, hsvd_dtype in_dtype, const hsvd_options* opts) {
+  if (!out) return HSVD_EINVAL;
+  *out = nullptr;
+  if (!hsvd::valid_dims(batch, m, n)) return HSVD_EINVAL;
+  if (block_rows < 1 || block_cols < 1 || block_rows > (1 << 30) || block_cols > (1 << 30)) return HSVD_EINVAL;
+  if (rank_cap < 1 || rank_cap > 256) return HSVD_EINVAL;
+  if (!(std::isfinite(param))) return HSVD_EINVAL;
+  switch (mode) {
+    case HSVD_TRUNC_FIXED_K:
+      if (param < 1 || param > 256 || param != std::floor(param)) return HSVD_EINVAL;
+      break;
+    case HSVD_TRUNC_GAMMA:
+      if (!(param > 0 && param < 1)) return HSVD_EINVAL;
+      break;
+    case HSVD_TRUNC_ENERGY:
+      if (!(param > 0 && param <= 1)) return HSVD_EINVAL;
+      break;
+    default: return HSVD_EINVAL;
+  }
+  if (tree != HSVD_TREE_COL_THEN_ROW && tree != HSVD_TREE_ROW_THEN_COL) return HSVD_EINVAL;
+  switch (prec) {
+    case HSVD_PREC_F64:
+      if (in_dtype != HSVD_DTYPE_F64) return HSVD_EINVAL;
+      break;
+    case HSVD_PREC_F32:
+      if (in_dtype != HSVD_DTYPE_F32) return HSVD_EINVAL;
+      break;
+    case HSVD_PREC_BF16_MIXED:
+      if (in_dtype != HSVD_DTYPE_F32 && in_dtype != HSVD_DTYPE_BF16) return HSVD_EINVAL;
+      break;
+    default: return HSVD_EINVAL;
+  }
+  hsvd_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.oversample < 0 || o.power_iters < -1 || o.max_sweeps < 0 || std::isnan(o.rank_tol)) return HSVD_EINVAL;
+
+  std::unique_ptr<hsvd_plan_s> h(new (std::nothrow) hsvd_plan_s());
+  if (!h) return HSVD_ENOMEM;
+  PlanImpl& P = h->impl;
+  P.batch = batch;
+  P.m.assign(m, m + batch);
+  P.n.assign(n, n + batch);
+  P.br = block_rows;
+  P.bc = block_cols;
+  P.mode = mode;
+  P.param = param;
+  P.rank_cap = rank_cap;
+  P.tree = tree;
+  P.prec = prec;
+  P.in_dtype = in_dtype;
+  const int base_k = mode == HSVD_TRUNC_FIXED_K ? (int)param : rank_cap;
+  P.kcap = std::min(rank_cap, base_k);
+  P.kp = std::min(256, base_k + (o.oversample > 0 ? o.oversample : base_k));
+  P.kp = std::max(P.kp, P.kcap);
+  P.q = o.power_iters == 0 ? (prec == HSVD_PREC_F64 ? 3 : 2) : (o.power_iters < 0 ? 0 : o.power_iters);
+  P.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
+  P.rank_tol = o.rank_tol > 0 ? o.rank_tol : (prec == HSVD_PREC_F64 ? 1e-12 : 1e-5);
+  P.seed = o.seed ? o.seed : 0x1710028ull;
+  P.host_staging = o.host_staging != 0;
+  P.elem = prec == HSVD_PREC_F64 ? 8 : 4;
+  P.in_elem = in_dtype == HSVD_DTYPE_F64 ? 8 : (in_dtype == HSVD_DTYPE_F32 ? 4 : 2);
+  P.tau = 50.0 * (prec == HSVD_PREC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+
+  if (cudaGetDevice(&P.dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ECUDA;
+  }
+  if (cudaMalloc(&P.d_mats, sizeof(hsvd::MatRef) * batch) != cudaSuccess ||
+      cudaMalloc(&P.d_status, sizeof(hsvd::DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  if (cudaMallocHost(&P.h_mats, sizeof(hsvd::MatRef) * batch) != cudaSuccess) {
+    P.h_mats = nullptr;
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&P.mats_done, cudaEventDisableTiming) != cudaSuccess) return HSVD_ECUDA;
+  if (cudaMemset(P.d_status, 0, sizeof(hsvd::DevStatus)) != cudaSuccess) return HSVD_ECUDA;
+  if (prec == HSVD_PREC_BF16_MIXED && in_dtype == HSVD_DTYPE_F32) {
+    for (int b = 0; b < batch; ++b) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, (size_t)m[b] * n[b] * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return HSVD_ENOMEM;
+      }
+      P.conv.push_back(p);
+    }
+  }
+  if (P.host_staging) {
+    for (int b = 0; b < batch; ++b) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, (size_t)m[b] * n[b] * P.in_elem) != cudaSuccess) {
+        cudaGetLastError();
+        return HSVD_ENOMEM;
+      }
+      P.staging.push_back(p);
+    }
+  }
+  hsvd_status st;
+  if (prec == HSVD_PREC_F64)
+    st = hsvd::build_plan<double, double>(P);
+  else if (prec == HSVD_PREC_F32)
+    st = hsvd::build_plan<float, float>(P);
+  else
+    st = hsvd::build_plan<float, __nv_bfloat16>(P);
+  if (st != HSVD_OK) return st;
+  *out = h.release();
+  return HSVD_OK;
+}
+
+static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_t* lda, cudaStream_t s) {
+  PlanImpl& P = plan->impl;
+  if (cudaEventSynchronize(P.mats_done) != cudaSuccess) return HSVD_ECUDA;
+  const bool conv = !P.conv.empty();
+  for (int b = 0; b < P.batch; ++b) {
+    if (conv) {
+      P.h_mats[b].ptr = P.conv[b];
+      P.h_mats[b].ld = P.n[b];
+    } else {
+      P.h_mats[b].ptr = A[b];
+      P.h_mats[b].ld = lda[b];
+    }
+  }
+  if (cudaMemcpyAsync(P.d_mats, P.h_mats, sizeof(hsvd::MatRef) * P.batch, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return HSVD_ECUDA;
+  if (cudaEventRecord(P.mats_done, s) != cudaSuccess) return HSVD_ECUDA;
+  if (cudaMemsetAsync(P.d_status, 0, sizeof(hsvd::DevStatus), s) != cudaSuccess) return HSVD_ECUDA;
+  if (conv)
+    for (int b = 0; b < P.batch; ++b)
+      if (hsvd::launch_f32_to_bf16(static_cast<const float*>(A[b]), lda[b], static_cast<__nv_bfloat16*>(P.conv[b]),
+                                   P.n[b], P.m[b], P.n[b], s) != cudaSuccess)
+        return HSVD_ECUDA;
+  for (auto& st : P.steps) {
+    if (st.run(s) != cudaSuccess) {
+      cudaGetLastError();
+      return HSVD_ECUDA;
+    }
+  }
+  P.ran = true;
+  P.last_stream = s;
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_run(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream) {
+  if (!plan || !A || !lda) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  for (int b = 0; b < P.batch; ++b)
+    if (!A[b] || lda[b] < P.n[b]) return HSVD_EINVAL;
+  return run_impl(plan, A, lda, static_cast<cudaStream_t>(stream));
+}
+
+hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream) {
+  if (!plan || !A || !lda) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (!P.host_staging) return HSVD_EINVAL;
+  for (int b = 0; b < P.batch; ++b)
+    if (!A[b] || lda[b] < P.n[b]) return HSVD_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const void*> dptr(P.batch);
+  std::vector<int64_t> dld(P.batch);
+  for (int b = 0; b < P.batch; ++b) {
+    const size_t w = (size_t)P.n[b] * P.in_elem;
+    if (cudaMemcpy2DAsync(P.staging[b], w, A[b], (size_t)lda[b] * P.in_elem, w, (size_t)P.m[b],
+                          cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return HSVD_ECUDA;
+    }
+    dptr[b] = P.staging[b];
+    dld[b] = P.n[b];
+  }
+  return run_impl(plan, dptr.data(), dld.data(), s);
+}
+
+hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r) {
+  if (!plan || !r) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (sync && P.ran && cudaStreamSynchronize(P.last_stream) != cudaSuccess) return HSVD_ECUDA;
+  hsvd::DevStatus ds;
+  if (cudaMemcpy(&ds, P.d_status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return HSVD_ECUDA;
+  r->not_converged = ds.not_converged;
+  r->chol_dropped = ds.chol_dropped;
+  r->nonfinite = ds.nonfinite;
+  r->min_rank = 0;
+  r->max_rank = 0;
+  if (P.ran) {
+    int mn = 1 << 30, mx = 0;
+    for (auto& o : P.outs) {
+      int rk = 0;
+      if (cudaMemcpy(&rk, o.rank, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HSVD_ECUDA;
+      mn = std::min(mn, rk);
+      mx = std::max(mx, rk);
+    }
+    r->min_rank = mn;
+    r->max_rank = mx;
+  }
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_factors(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* U, int64_t ldu, void* S, void* V,
+                         int64_t ldv, hsvd_where where, void* stream) {
+  if (!plan) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (idx < 0 || idx >= P.batch) return HSVD_EINVAL;
+  if (where != HSVD_WHERE_HOST && where != HSVD_WHERE_DEVICE) return HSVD_EINVAL;
+  const int64_t mo = P.m[idx], no = P.n[idx];
+  if (U && ldu < mo) return HSVD_EINVAL;
+  if (V && ldv < no) return HSVD_EINVAL;
+  if (!P.ran) return HSVD_ENOTREADY;
+  const auto& po = P.outs[idx];
+  // original orientation: U_orig (m rows), V_orig (n rows)
+  void* su = po.trans ? po.V : po.U;
+  void* sv = po.trans ? po.U : po.V;
+  const int kc = P.kcap;
+  const size_t el = P.elem;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (where == HSVD_WHERE_DEVICE) {
+    cudaError_t e = cudaSuccess;
+    if (U)
+      e = (el == 8) ? hsvd::launch_rowmajor_to_colmajor<double>(static_cast<double*>(su), kc, (int)mo, po.rank, kc,
+                                                                static_cast<double*>(U), ldu, s)
+                    : hsvd::launch_rowmajor_to_colmajor<float>(static_cast<float*>(su), kc, (int)mo, po.rank, kc,
+                                                               static_cast<float*>(U), ldu, s);
+    if (e == cudaSuccess && V)
+      e = (el == 8) ? hsvd::launch_rowmajor_to_colmajor<double>(static_cast<double*>(sv), kc, (int)no, po.rank, kc,
+                                                                static_cast<double*>(V), ldv, s)
+                    : hsvd::launch_rowmajor_to_colmajor<float>(static_cast<float*>(sv), kc, (int)no, po.rank, kc,
+                                                               static_cast<float*>(V), ldv, s);
+    if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, po.sig, el * kc, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && rank) {
+      int rk = 0;
+      e = cudaMemcpyAsync(&rk, po.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      *rank = rk;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return HSVD_ECUDA;
+    }
+    return HSVD_OK;
+  }
+  int rk = 0;
+  std::vector<char> hu, hv;
+  cudaError_t e = cudaMemcpyAsync(&rk, po.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && U) {
+    hu.resize((size_t)mo * kc * el);
+    e = cudaMemcpyAsync(hu.data(), su, hu.size(), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess && V) {
+    hv.resize((size_t)no * kc * el);
+    e = cudaMemcpyAsync(hv.data(), sv, hv.size(), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, po.sig, el * kc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ECUDA;
+  }
+  rk = std::max(0, std::min(rk, kc));
+  if (rank) *rank = rk;
+  auto transpose = [&](const std::vector<char>& src, int64_t rows, void* dst, int64_t ldd) {
+    for (int c = 0; c < rk; ++c)
+      for (int64_t i = 0; i < rows; ++i)
+        std::memcpy(static_cast<char*>(dst) + (c * ldd + i) * el, src.data() + (i * kc + c) * el, el);
+  };
+  if (U) transpose(hu, mo, U, ldu);
+  if (V) transpose(hv, no, V, ldv);
+  return HSVD_OK;
+}
+
+int64_t hsvd_workspace_bytes(hsvd_plan_t plan) {
+  if (!plan) return 0;
+  const PlanImpl& P = plan->impl;
+  int64_t t = (int64_t)P.arena_bytes + (int64_t)P.tables_bytes;
+  for (size_t b = 0; b < P.conv.size(); ++b) t += P.m[b] * P.n[b] * 2;
+  for (size_t b = 0; b < P.staging.size(); ++b) t += P.m[b] * P.n[b] * (int64_t)P.in_elem;
+  return t;
+}
+
+int32_t hsvd_launches_per_run(hsvd_plan_t plan) {
+  if (!plan) return -1;
+  const PlanImpl& P = plan->impl;
+  return P.launches_per_run + (P.conv.empty() ? 0 : P.batch);
+}
+
+void hsvd_destroy(hsvd_plan_t plan) { delete plan; }
+
+}  // extern "C"

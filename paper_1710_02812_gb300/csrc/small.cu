@@ -1,0 +1,598 @@
+// Per-task small-matrix kernels of the path (one CTA per task, batched over
+// a whole tree level):
+//
+//  * k_chol     Cholesky of a Gram matrix with relative pivot dropping and an
+//               explicit inverse of the factor (CholeskyQR, used to
+//               orthonormalise the sketch Y, the power-step W, the merge
+//               complement Q = U2 - U1 P (Section 3, "If Q = U_o R") and the
+//               slab / final projections).
+//  * k_jacobi   one-sided (Hestenes) Jacobi SVD of a small core: the block
+//               core R^T, the merge core E of Eq. orthmerge1 (built on the
+//               fly), the slab core, the final projection core; sorts the
+//               singular values, applies the truncation rule (Section 3,
+//               MAT) and writes the left singular vectors.
+//  * helpers    sketch-matrix generator, FP32 -> BF16 conversion, per-block
+//               energies, sign normalisation and layout conversion.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hsvd {
+
+namespace {
+
+template <class T>
+struct Eps;
+template <>
+struct Eps<float> {
+  static constexpr double v = 5.9604644775390625e-08;
+};
+template <>
+struct Eps<double> {
+  static constexpr double v = 1.1102230246251565e-16;
+};
+
+template <class T>
+__device__ __forceinline__ T dsqrt(T x) {
+  return sqrt(x);
+}
+
+// ------------------------------------------------------------------ Cholesky
+// In-place elimination on the unit-diagonal scaled Gram matrix Gh = S G S:
+// the upper triangle (incl. diagonal) holds the trailing Gram entries and
+// finally the unit-row factor U = D L^T; the strictly lower triangle holds
+// the unit lower inverse L^{-1}.  R = D^{-1/2} U S^{-1}, R^{-1} = S L^{-T} D^{-1/2}.
+template <class T>
+__global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ tasks, int kcap,
+                                              DevStatus* __restrict__ st, T tau, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T sc[256];
+  __shared__ T dpv[256];
+  const CholTask<T>& tk = tasks[blockIdx.x];
+  const int k = eff(tk.k);
+  if (k <= 0) return;
+  T* M = use_smem ? reinterpret_cast<T*>(smem_raw) : tk.work;
+  const int ld = k;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = tid; j < k; j += nt) {
+    const T g = tk.G[(int64_t)j * tk.ldg + j];
+    if (!isfinite(g)) bad = 1;
+    sc[j] = (g > T(0) && isfinite(g)) ? T(1) / dsqrt(g) : T(0);
+  }
+  __syncthreads();
+  if (tid == 0 && bad && st) atomicAdd(&st->nonfinite, 1);
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e % k;
+    M[i * ld + j] = (j >= i) ? tk.G[(int64_t)i * tk.ldg + j] * sc[i] * sc[j] : T(0);
+  }
+  __syncthreads();
+
+  int ndrop = 0;
+  for (int j = 0; j < k; ++j) {
+    const T d = M[j * ld + j];
+    const bool drop = !(sc[j] > T(0)) || !(d > tau);
+    __syncthreads();  // every thread has read d before row j+1.. are touched
+    if (drop) {
+      if (tid == 0) dpv[j] = T(0);
+      ++ndrop;
+      continue;
+    }
+    if (tid == 0) dpv[j] = d;
+    const T dinv = T(1) / d;
+    const int rows = k - j - 1;
+    for (int e = tid; e < rows * k; e += nt) {
+      const int i = j + 1 + e / k;
+      const int c = e % k;
+      const T f = M[j * ld + i] * dinv;
+      if (c >= i) {
+        M[i * ld + c] -= f * M[j * ld + c];
+      } else if (c < j) {
+        M[i * ld + c] -= f * M[j * ld + c];
+      } else if (c == j) {
+        M[i * ld + j] = -f;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0 && ndrop > 0 && st) atomicAdd(&st->chol_dropped, ndrop);
+
+  // R^{-1}[l][j] = s_l * Linv[j][l] / sqrt(d_j)  (l <= j, Linv[j][j] = 1)
+  if (tk.Rinv) {
+    for (int e = tid; e < k * k; e += nt) {
+      const int l = e / k, j = e % k;
+      T v = T(0);
+      if (l <= j && dpv[j] > T(0)) {
+        const T lij = (l == j) ? T(1) : M[j * ld + l];
+        v = sc[l] * lij / dsqrt(dpv[j]);
+      }
+      tk.Rinv[(int64_t)l * tk.ldri + j] = v;
+    }
+  }
+  __syncthreads();
+  // R[j][c] = M[j][c] / sqrt(d_j) / s_c  (c >= j), in place in the upper part.
+  for (int e = tid; e < k * k; e += nt) {
+    const int j = e / k, c = e % k;
+    T v = T(0);
+    if (c >= j && dpv[j] > T(0) && sc[c] > T(0)) v = M[j * ld + c] / dsqrt(dpv[j]) / sc[c];
+    M[j * ld + c] = v;
+  }
+  __syncthreads();
+  if (!tk.R) return;
+  if (tk.Rprev) {
+    for (int e = tid; e < k * k; e += nt) {
+      const int i = e / k, j = e % k;
+      T s = T(0);
+      if (j >= i)
+        for (int l = i; l <= j; ++l) s += M[i * ld + l] * tk.Rprev[(int64_t)l * tk.ldrp + j];
+      tk.R[(int64_t)i * tk.ldr + j] = s;
+    }
+  } else {
+    for (int e = tid; e < k * k; e += nt) {
+      const int i = e / k, j = e % k;
+      tk.R[(int64_t)i * tk.ldr + j] = M[i * ld + j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Round-robin (circle) ordering for n even: slot 0 pairs (r, n-1); slot s>0
+// pairs (r+s, r-s) mod (n-1).  Each unordered pair appears once per sweep and
+// the pairs of one round are disjoint.
+__host__ __device__ __forceinline__ void rr_pair(int n, int r, int s, int& p, int& q) {
+  const int m = n - 1;
+  if (s == 0) {
+    p = r;
+    q = m;
+  } else {
+    p = (r + s) % m;
+    q = (r - s + m) % m;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
+  for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+  return v;
+}
+
+template <class T, bool WANT_V>
+__global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict__ tasks, int nrcap, int nccap,
+                                                TruncParams tp, DevStatus* __restrict__ st, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T sig_s[512];
+  __shared__ int perm[512];
+  __shared__ int rank_s;
+  const JacobiTask<T>& tk = tasks[blockIdx.x];
+  int nr, nc, k1 = 0, k2 = 0;
+  if (tk.load == 1) {
+    k1 = eff(tk.k1);
+    k2 = eff(tk.k2);
+    nr = nc = k1 + k2;
+  } else {
+    nr = eff(tk.nr);
+    nc = eff(tk.nc);
+  }
+  const int n = nc + (nc & 1);
+  const int ncc = nccap + (nccap & 1);
+  T* Mw = use_smem ? reinterpret_cast<T*>(smem_raw) : tk.work;
+  T* Vw = WANT_V ? (Mw + (int64_t)nrcap * ncc) : nullptr;
+  const int ldm = nr > 0 ? nr : 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // ---- load (column-major working copy)
+  for (int e = tid; e < nr * n; e += nt) {
+    const int i = e % nr, j = e / nr;
+    T v = T(0);
+    if (j < nc) {
+      if (tk.load == 0) {
+        v = tk.src[(int64_t)i * tk.rs + (int64_t)j * tk.cs];
+      } else if (i < k1) {
+        if (j < k1)
+          v = (i == j) ? tk.s1[i] : T(0);
+        else {
+          T p = tk.P[(int64_t)i * tk.ldp + (j - k1)];
+          if (tk.P2) p += tk.P2[(int64_t)i * tk.ldp + (j - k1)];
+          v = p * tk.s2[j - k1];
+        }
+      } else if (j >= k1) {
+        v = tk.R[(int64_t)(i - k1) * tk.ldr + (j - k1)] * tk.s2[j - k1];
+      }
+    }
+    Mw[(int64_t)j * ldm + i] = v;
+  }
+  if (WANT_V)
+    for (int e = tid; e < n * n; e += nt) Vw[e] = ((e / n) == (e % n)) ? T(1) : T(0);
+  __syncthreads();
+
+  // ---- sweeps
+  const int G = nr >= 128 ? 32 : (nr >= 64 ? 16 : (nr >= 24 ? 8 : 4));
+  const int ngroups = nt / G;
+  const int gid = tid / G, lane = tid % G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) / G * G));
+  const T tol = T(4.0 * Eps<T>::v * sqrt((double)(nr > 1 ? nr : 1)));
+  int sweep = 0;
+  bool converged = (n <= 1);
+  for (; sweep < tp.max_sweeps && !converged; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      for (int slot = gid; slot < n / 2; slot += ngroups) {
+        int p, q;
+        rr_pair(n, r, slot, p, q);
+        if (p >= nc || q >= nc) continue;
+        T* x = Mw + (int64_t)p * ldm;
+        T* y = Mw + (int64_t)q * ldm;
+        T a = T(0), b = T(0), c = T(0);
+        for (int i = lane; i < nr; i += G) {
+          const T xi = x[i], yi = y[i];
+          a += xi * xi;
+          b += yi * yi;
+          c += xi * yi;
+        }
+        a = group_sum(a, G, gmask);
+        b = group_sum(b, G, gmask);
+        c = group_sum(c, G, gmask);
+        if (c != T(0) && fabs(c) > tol * dsqrt(a) * dsqrt(b)) {
+          const T zeta = (b - a) / (T(2) * c);
+          const T az = fabs(zeta);
+          T t;
+          if (az > T(1)) {
+            const T iz = T(1) / az;
+            t = T(1) / (az * (T(1) + dsqrt(T(1) + iz * iz)));
+          } else {
+            t = T(1) / (az + dsqrt(T(1) + az * az));
+          }
+          if (zeta < T(0)) t = -t;
+          const T cs = T(1) / dsqrt(T(1) + t * t);
+          const T sn = cs * t;
+          for (int i = lane; i < nr; i += G) {
+            const T xi = x[i], yi = y[i];
+            x[i] = cs * xi - sn * yi;
+            y[i] = sn * xi + cs * yi;
+          }
+          if (WANT_V) {
+            T* vx = Vw + (int64_t)p * n;
+            T* vy = Vw + (int64_t)q * n;
+            for (int i = lane; i < nc; i += G) {
+              const T xi = vx[i], yi = vy[i];
+              vx[i] = cs * xi - sn * yi;
+              vy[i] = sn * xi + cs * yi;
+            }
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    converged = !__syncthreads_or(rotated);
+  }
+  if (!converged && tid == 0 && st) atomicAdd(&st->not_converged, 1);
+
+  // ---- singular values = column norms, sorted descending
+  for (int j = gid; j < nc; j += ngroups) {
+    const T* x = Mw + (int64_t)j * ldm;
+    T a = T(0);
+    for (int i = lane; i < nr; i += G) a += x[i] * x[i];
+    a = group_sum(a, G, gmask);
+    if (lane == 0) sig_s[j] = isfinite(a) ? dsqrt(a) : T(-1);
+  }
+  __syncthreads();
+  for (int j = tid; j < nc; j += nt) {
+    const T sj = sig_s[j];
+    int pos = 0;
+    for (int i = 0; i < nc; ++i) {
+      const T si = sig_s[i];
+      pos += (si > sj) || (si == sj && i < j);
+    }
+    perm[pos] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int bad = 0;
+    for (int i = 0; i < nc; ++i) bad += sig_s[i] < T(0);
+    if (bad && st) atomicAdd(&st->nonfinite, 1);
+    int r = 0;
+    const double s1 = nc > 0 ? (double)sig_s[perm[0]] : 0.0;
+    if (nc > 0 && s1 > 0.0 && !bad) {
+      int numerical = 0;
+      for (int i = 0; i < nc; ++i) numerical += (double)sig_s[perm[i]] > tp.rank_tol * s1;
+      if (tp.mode == 0) {
+        r = (int)tp.param;
+      } else if (tp.mode == 1) {
+        r = 0;
+        for (int i = 0; i < nc; ++i) r += (double)sig_s[perm[i]] >= tp.param * s1;
+      } else {
+        double total = 0.0;
+        if (tk.energy) {
+          total = (double)*tk.energy;
+        } else if (tk.load == 1) {
+          for (int i = 0; i < k1; ++i) total += (double)tk.s1[i] * (double)tk.s1[i];
+          for (int i = 0; i < k2; ++i) total += (double)tk.s2[i] * (double)tk.s2[i];
+        } else {
+          for (int i = 0; i < nc; ++i) total += (double)sig_s[i] * (double)sig_s[i];
+        }
+        double cum = 0.0;
+        r = nc;
+        for (int i = 0; i < nc; ++i) {
+          const double s = (double)sig_s[perm[i]];
+          cum += s * s;
+          if (cum >= tp.param * total) {
+            r = i + 1;
+            break;
+          }
+        }
+      }
+      r = min(r, numerical);
+      r = min(r, tp.rank_cap);
+      r = min(r, nc);
+      r = min(r, tk.ucap);
+      if (r < 0) r = 0;
+    }
+    rank_s = r;
+    if (tk.rank) *tk.rank = r;
+  }
+  __syncthreads();
+  const int r = rank_s;
+  if (tk.sig)
+    for (int c = tid; c < tk.ucap; c += nt) tk.sig[c] = (c < r) ? sig_s[perm[c]] : T(0);
+  if (tk.U) {
+    for (int e = tid; e < nr * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      T v = T(0);
+      if (c < r) v = Mw[(int64_t)perm[c] * ldm + i] / sig_s[perm[c]];
+      tk.U[(int64_t)i * tk.ldu + c] = v;
+    }
+  }
+  if (WANT_V && tk.V) {
+    for (int e = tid; e < nc * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * n + i] : T(0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+// splitmix64 (Steele, Lea & Flood, 2014) as a counter-based generator, and a
+// Box-Muller transform of two of its outputs per element.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_fill_gaussian(T* out, int64_t count, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)e));
+    const uint64_t b = splitmix64(seed ^ (2 * (uint64_t)e + 1));
+    const double u1 = ((double)(a >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
+    const double u2 = (double)(b >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    out[e] = (T)z;
+  }
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    dst[i * ldd + j] = __float2bfloat16_rn(src[i * lds + j]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ float to_f(T x) {
+  return (float)x;
+}
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+// ||X_blk||_F^2 with per-thread compensated (Kahan) FP32 sums and a
+// fixed-order FP64 combination of the per-thread partials.
+template <class TA, class TO>
+__global__ void __launch_bounds__(256) k_block_energy(const EnergyTask* __restrict__ tasks,
+                                                      const MatRef* __restrict__ mats) {
+  __shared__ double part[256];
+  const EnergyTask tk = tasks[blockIdx.x];
+  const MatRef mr = mats[tk.mat];
+  const TA* A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+  float s = 0.f, comp = 0.f;
+  const int64_t total = (int64_t)tk.h * tk.w;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t i = e / tk.w, j = e % tk.w;
+    const float v = to_f(A[i * mr.ld + j]);
+    const float y = v * v - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  part[threadIdx.x] = (double)s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) acc += part[i];
+    *static_cast<TO*>(tk.out) = (TO)acc;
+  }
+}
+
+// One CTA per column c < rank: find the first row of largest |U[i][c]|, flip
+// the column of U and of V if that entry is negative.
+template <class T>
+__global__ void __launch_bounds__(256) k_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n,
+                                                        const int* rank) {
+  __shared__ T bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.x;
+  if (c >= *rank) return;
+  T best = T(-1);
+  int besti = 0x7fffffff;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T a = fabs(U[(int64_t)i * ldu + c]);
+    if (a > best || (a == best && i < besti)) {
+      best = a;
+      besti = i;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = besti;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      const T ob = bv[threadIdx.x + off];
+      const int oi = bi[threadIdx.x + off];
+      if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = ob;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int imax = bi[0];
+  if (imax >= m) return;
+  const bool neg = U[(int64_t)imax * ldu + c] < T(0);
+  __syncthreads();
+  if (!neg) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) U[(int64_t)i * ldu + c] = -U[(int64_t)i * ldu + c];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * ldv + c] = -V[(int64_t)i * ldv + c];
+}
+
+template <class T>
+__global__ void k_rm_to_cm(const T* __restrict__ src, int64_t lds, int rows, const int* rank, int kcap,
+                           T* __restrict__ dst, int64_t ldd) {
+  const int r = min(*rank, kcap);
+  const int64_t total = (int64_t)rows * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, i = e % rows;
+    dst[c * ldd + i] = src[i * lds + c];
+  }
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int jacobi_pair_host(int n, int r, int s, int* p, int* q) {
+  if (n < 2 || (n & 1) || r < 0 || r >= n - 1 || s < 0 || s >= n / 2) return 1;
+  rr_pair(n, r, s, *p, *q);
+  return 0;
+}
+
+template <class T>
+cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
+                        cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (kcap > 256) return cudaErrorInvalidValue;
+  const size_t bytes = (size_t)kcap * kcap * sizeof(T);
+  const int use_smem = bytes <= 200 * 1024;
+  if (use_smem && bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  k_chol<T><<<ntasks, 256, use_smem ? bytes : 0, s>>>(tasks, kcap, st, (T)tau, use_smem);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                          TruncParams tp, DevStatus* st, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (nccap > 512 || nrcap > 512) return cudaErrorInvalidValue;
+  const size_t bytes = jacobi_work_bytes(nrcap, nccap, want_v, sizeof(T));
+  const int use_smem = bytes <= 200 * 1024;
+  const int threads = (nrcap >= 64 || nccap >= 64) ? 512 : 256;
+  cudaError_t e = cudaSuccess;
+  if (want_v) {
+    if (use_smem && bytes > 48 * 1024)
+      e = cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_jacobi<T, true><<<ntasks, threads, use_smem ? bytes : 0, s>>>(tasks, nrcap, nccap, tp, st, use_smem);
+  } else {
+    if (use_smem && bytes > 48 * 1024)
+      e = cudaFuncSetAttribute(k_jacobi<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_jacobi<T, false><<<ntasks, threads, use_smem ? bytes : 0, s>>>(tasks, nrcap, nccap, tp, st, use_smem);
+  }
+  return cudaGetLastError();
+}
+
+size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem) {
+  const int ncc = nccap + (nccap & 1);
+  return ((size_t)nrcap * ncc + (want_v ? (size_t)ncc * ncc : 0)) * elem;
+}
+bool jacobi_uses_smem(int nrcap, int nccap, bool want_v, size_t elem) {
+  return jacobi_work_bytes(nrcap, nccap, want_v, elem) <= 200 * 1024;
+}
+bool chol_uses_smem(int kcap, size_t elem) { return (size_t)kcap * kcap * elem <= 200 * 1024; }
+
+cudaError_t launch_fill_gaussian_f32(float* out, int64_t count, uint64_t seed, cudaStream_t s) {
+  k_fill_gaussian<float><<<grid_for(count, 256), 256, 0, s>>>(out, count, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_gaussian_f64(double* out, int64_t count, uint64_t seed, cudaStream_t s) {
+  k_fill_gaussian<double><<<grid_for(count, 256), 256, 0, s>>>(out, count, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, int64_t ldd, int64_t rows,
+                               int64_t cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_f32_to_bf16<<<grid_for(rows * cols, 256), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  return cudaGetLastError();
+}
+
+template <class TA, class TO>
+cudaError_t launch_block_energy(const EnergyTask* tasks, int ntasks, const MatRef* mats, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_block_energy<TA, TO><<<ntasks, 256, 0, s>>>(tasks, mats);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n, const int* rank, int kcap,
+                                  cudaStream_t s) {
+  if (kcap <= 0) return cudaSuccess;
+  k_sign_normalise<T><<<kcap, 256, 0, s>>>(U, ldu, m, V, ldv, n, rank);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_rowmajor_to_colmajor(const T* src, int64_t lds, int rows, const int* rank, int kcap, T* dst,
+                                        int64_t ldd, cudaStream_t s) {
+  k_rm_to_cm<T><<<grid_for((int64_t)rows * kcap, 256), 256, 0, s>>>(src, lds, rows, rank, kcap, dst, ldd);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_chol<float>(const CholTask<float>*, int, int, DevStatus*, double, cudaStream_t);
+template cudaError_t launch_chol<double>(const CholTask<double>*, int, int, DevStatus*, double, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const JacobiTask<float>*, int, int, int, bool, TruncParams, DevStatus*,
+                                          cudaStream_t);
+template cudaError_t launch_jacobi<double>(const JacobiTask<double>*, int, int, int, bool, TruncParams,
+                                           DevStatus*, cudaStream_t);
+template cudaError_t launch_block_energy<float, float>(const EnergyTask*, int, const MatRef*, cudaStream_t);
+template cudaError_t launch_block_energy<double, double>(const EnergyTask*, int, const MatRef*, cudaStream_t);
+template cudaError_t launch_block_energy<__nv_bfloat16, float>(const EnergyTask*, int, const MatRef*,
+                                                               cudaStream_t);
+template cudaError_t launch_sign_normalise<float>(float*, int64_t, int, float*, int64_t, int, const int*, int,
+                                                  cudaStream_t);
+template cudaError_t launch_sign_normalise<double>(double*, int64_t, int, double*, int64_t, int, const int*, int,
+                                                   cudaStream_t);
+template cudaError_t launch_rowmajor_to_colmajor<float>(const float*, int64_t, int, const int*, int, float*,
+                                                        int64_t, cudaStream_t);
+template cudaError_t launch_rowmajor_to_colmajor<double>(const double*, int64_t, int, const int*, int, double*,
+                                                         int64_t, cudaStream_t);
+
+}  // namespace hsvd

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libhsvd (include/hsvd.h).
+
+Only argument marshalling lives here: every step of the path runs in the
+CUDA kernels of the shared library.  PyTorch supplies device memory and
+streams.  If the library has not been built the first call raises; there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhsvd.so")
+
+HSVD_OK, HSVD_EINVAL, HSVD_ENOMEM, HSVD_ECUDA, HSVD_ENOTREADY, HSVD_EUNSUPPORTED = range(6)
+TRUNC = {"fixed_k": 0, "gamma": 1, "energy": 2}
+TREE = {"col_then_row": 0, "row_then_col": 1}
+PREC = {"f64": 0, "f32": 1, "bf16_mixed": 2}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
+WHERE = {"host": 0, "device": 1}
+
+EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd_factors",
+            "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
+            "hsvd_tree_levels", "hsvd_jacobi_pair")
+
+
+class HsvdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (status {code})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+                ("rank_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("max_sweeps", ctypes.c_int32), ("host_staging", ctypes.c_int32)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("not_converged", ctypes.c_int32), ("chol_dropped", ctypes.c_int32),
+                ("nonfinite", ctypes.c_int32), ("min_rank", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load libhsvd.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA path has no fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.hsvd_plan.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(i64), ctypes.POINTER(i64), i64, i64,
+                                ctypes.c_int, dbl, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(Options)]
+        L.hsvd_plan.restype = ctypes.c_int
+        L.hsvd_run.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(i64), P]
+        L.hsvd_run.restype = ctypes.c_int
+        L.hsvd_run_host.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(i64), P]
+        L.hsvd_run_host.restype = ctypes.c_int
+        L.hsvd_status_query.argtypes = [P, i32, ctypes.POINTER(Report)]
+        L.hsvd_status_query.restype = ctypes.c_int
+        L.hsvd_factors.argtypes = [P, i32, ctypes.POINTER(i32), P, i64, P, P, i64, ctypes.c_int, P]
+        L.hsvd_factors.restype = ctypes.c_int
+        L.hsvd_workspace_bytes.argtypes = [P]
+        L.hsvd_workspace_bytes.restype = i64
+        L.hsvd_launches_per_run.argtypes = [P]
+        L.hsvd_launches_per_run.restype = i32
+        L.hsvd_destroy.argtypes = [P]
+        L.hsvd_destroy.restype = None
+        L.hsvd_error_string.argtypes = [ctypes.c_int]
+        L.hsvd_error_string.restype = ctypes.c_char_p
+        L.hsvd_tree_levels.argtypes = [i64]
+        L.hsvd_tree_levels.restype = i32
+        L.hsvd_jacobi_pair.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.hsvd_jacobi_pair.restype = ctypes.c_int
+        _lib_handle = L
+    return _lib_handle
+
+
+def error_string(code: int) -> str:
+    return lib().hsvd_error_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != HSVD_OK:
+        raise HsvdError(code, where)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+
+def hsvd_plan(m: Sequence[int], n: Sequence[int], block_rows: int, block_cols: int, mode: str = "fixed_k",
+              param: float = 10, rank_cap: int = 256, tree: str = "col_then_row", prec: str = "f32",
+              in_dtype: Optional[str] = None, options: Optional[Options] = None) -> ctypes.c_void_p:
+    """hsvd_plan(): returns the plan handle; raises HsvdError on failure."""
+    m = [int(v) for v in m]
+    n = [int(v) for v in n]
+    if len(m) != len(n):
+        raise ValueError("m and n must have the same length")
+    if in_dtype is None:
+        in_dtype = {"f64": "f64", "f32": "f32", "bf16_mixed": "f32"}[prec]
+    h = ctypes.c_void_p()
+    ma = (ctypes.c_int64 * max(1, len(m)))(*m)
+    na = (ctypes.c_int64 * max(1, len(n)))(*n)
+    code = lib().hsvd_plan(ctypes.byref(h), len(m), ma, na, int(block_rows), int(block_cols), TRUNC[mode],
+                           float(param), int(rank_cap), TREE[tree], PREC[prec], DTYPE[in_dtype],
+                           ctypes.byref(options) if options is not None else None)
+    _check(code, "hsvd_plan")
+    return h
+
+
+def hsvd_run(plan, ptrs: Sequence[int], lda: Sequence[int], stream=None):
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    ld = (ctypes.c_int64 * len(lda))(*[int(v) for v in lda])
+    _check(lib().hsvd_run(plan, arr, ld, _stream_ptr(stream)), "hsvd_run")
+
+
+def hsvd_run_host(plan, ptrs: Sequence[int], lda: Sequence[int], stream=None):
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    ld = (ctypes.c_int64 * len(lda))(*[int(v) for v in lda])
+    _check(lib().hsvd_run_host(plan, arr, ld, _stream_ptr(stream)), "hsvd_run_host")
+
+
+def hsvd_status_query(plan, sync: bool = True) -> dict:
+    r = Report()
+    _check(lib().hsvd_status_query(plan, 1 if sync else 0, ctypes.byref(r)), "hsvd_status_query")
+    return r.as_dict()
+
+
+def hsvd_factors(plan, idx, rank_p, U, ldu, S, V, ldv, where, stream):
+    return lib().hsvd_factors(plan, idx, rank_p, U, ldu, S, V, ldv, where, stream)
+
+
+def hsvd_workspace_bytes(plan) -> int:
+    return int(lib().hsvd_workspace_bytes(plan))
+
+
+def hsvd_launches_per_run(plan) -> int:
+    return int(lib().hsvd_launches_per_run(plan))
+
+
+def hsvd_destroy(plan):
+    lib().hsvd_destroy(plan)
+
+
+def hsvd_tree_levels(count: int) -> int:
+    return int(lib().hsvd_tree_levels(int(count)))
+
+
+def hsvd_jacobi_pair(n: int, rnd: int, slot: int):
+    p, q = ctypes.c_int32(), ctypes.c_int32()
+    code = lib().hsvd_jacobi_pair(n, rnd, slot, ctypes.byref(p), ctypes.byref(q))
+    if code != HSVD_OK:
+        raise HsvdError(code, "hsvd_jacobi_pair")
+    return p.value, q.value
+
+
+# ------------------------------------------------------------------ wrapper
+
+class Plan:
+    """Owning wrapper around an hsvd plan."""
+
+    def __init__(self, m, n, block_rows, block_cols, mode="fixed_k", param=10, rank_cap=None,
+                 tree="col_then_row", prec="f32", in_dtype=None, oversample=0, power_iters=0,
+                 rank_tol=0.0, seed=0, max_sweeps=0, host_staging=False):
+        if isinstance(m, int):
+            m, n = [m], [n]
+        if rank_cap is None:
+            rank_cap = int(param) if mode == "fixed_k" else 128
+        self.m, self.n = list(m), list(n)
+        self.prec = prec
+        self.in_dtype = in_dtype or {"f64": "f64", "f32": "f32", "bf16_mixed": "f32"}[prec]
+        self.rank_cap = int(rank_cap)
+        self.kcap = min(self.rank_cap, int(param) if mode == "fixed_k" else self.rank_cap)
+        opts = Options(int(oversample), int(power_iters), float(rank_tol), int(seed), int(max_sweeps),
+                       1 if host_staging else 0)
+        self._h = hsvd_plan(self.m, self.n, block_rows, block_cols, mode, param, self.rank_cap, tree, prec,
+                            self.in_dtype, opts)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            hsvd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def factor_dtype(self):
+        return np.float64 if self.prec == "f64" else np.float32
+
+    def run(self, mats, stream=None):
+        """mats: list of CUDA tensors (row-major, contiguous rows)."""
+        ptrs = [t.data_ptr() for t in mats]
+        lda = [t.stride(0) for t in mats]
+        hsvd_run(self._h, ptrs, lda, stream)
+
+    def run_host(self, arrays, stream=None):
+        """arrays: list of host arrays (numpy or CPU tensors)."""
+        ptrs, lda = [], []
+        for a in arrays:
+            if isinstance(a, np.ndarray):
+                ptrs.append(a.ctypes.data)
+                lda.append(a.strides[0] // a.itemsize)
+            else:
+                ptrs.append(a.data_ptr())
+                lda.append(a.stride(0))
+        hsvd_run_host(self._h, ptrs, lda, stream)
+
+    def factors(self, idx=0, stream=None):
+        """Copy (U, S, V) of matrix idx to host numpy arrays (column-major
+        in the library, returned as ordinary m x r / n x r arrays)."""
+        dt = self.factor_dtype
+        m, n, kc = self.m[idx], self.n[idx], self.kcap
+        U = np.zeros((kc, m), dtype=dt)  # column-major m x kc == row-major kc x m
+        V = np.zeros((kc, n), dtype=dt)
+        S = np.zeros(kc, dtype=dt)
+        r = ctypes.c_int32()
+        code = hsvd_factors(self._h, idx, ctypes.byref(r), U.ctypes.data, m, S.ctypes.data, V.ctypes.data, n,
+                            WHERE["host"], _stream_ptr(stream))
+        _check(code, "hsvd_factors")
+        k = r.value
+        return U[:k].T.copy(), S[:k].copy(), V[:k].T.copy()
+
+    def factors_device(self, U, S, V, idx=0, stream=None) -> int:
+        """Write column-major factors into device tensors U (kcap x m storage),
+        S (kcap), V (kcap x n storage); returns the rank."""
+        r = ctypes.c_int32()
+        code = hsvd_factors(self._h, idx, ctypes.byref(r), U.data_ptr() if U is not None else None, self.m[idx],
+                            S.data_ptr() if S is not None else None, V.data_ptr() if V is not None else None,
+                            self.n[idx], WHERE["device"], _stream_ptr(stream))
+        _check(code, "hsvd_factors")
+        return r.value
+
+    def status(self, sync=True):
+        return hsvd_status_query(self._h, sync)
+
+    @property
+    def workspace_bytes(self):
+        return hsvd_workspace_bytes(self._h)
+
+    @property
+    def launches_per_run(self):
+        return hsvd_launches_per_run(self._h)

@@ -1,0 +1,122 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/hsvd.h, rejects invalid arguments before touching the
+device, and its host-side schedule helpers agree with the tree and Jacobi
+orderings they describe."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1710_02812_gb300 import hsvd
+from oracle import hmat as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(hsvd.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return hsvd.lib()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "hsvd.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsvd_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "hsvd_plan" in names and "hsvd_run" in names and "hsvd_factors" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(hsvd.EXPORTED)
+
+
+def test_error_strings(lib):
+    for code in range(6):
+        assert hsvd.error_string(code)
+    assert hsvd.error_string(0) == "success"
+
+
+@pytest.mark.parametrize("count", [1, 2, 3, 5, 7, 8, 64, 65, 1000])
+def test_tree_levels_match_merge_schedule(lib, count):
+    assert hsvd.hsvd_tree_levels(count) == len(H.tree_schedule(count))
+    assert hsvd.hsvd_tree_levels(0) == -1
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 20, 64, 128, 256])
+def test_jacobi_round_robin_covers_each_pair_once(lib, n):
+    seen = set()
+    for r in range(n - 1):
+        used = set()
+        for s in range(n // 2):
+            p, q = hsvd.hsvd_jacobi_pair(n, r, s)
+            assert 0 <= p < n and 0 <= q < n and p != q
+            assert p not in used and q not in used       # disjoint within a round
+            used.update((p, q))
+            pair = (min(p, q), max(p, q))
+            assert pair not in seen                      # once per sweep
+            seen.add(pair)
+    assert len(seen) == n * (n - 1) // 2
+
+
+def test_jacobi_pair_rejects_bad_arguments(lib):
+    for args in [(3, 0, 0), (4, 3, 0), (4, 0, 2), (0, 0, 0)]:
+        with pytest.raises(hsvd.HsvdError):
+            hsvd.hsvd_jacobi_pair(*args)
+
+
+def _plan_code(lib, batch=1, m=(64,), n=(64,), br=16, bc=16, mode=0, param=4.0, cap=8, tree=0, prec=1, dt=1,
+               opts=None):
+    h = ctypes.c_void_p(1234)
+    ma = (ctypes.c_int64 * max(1, len(m)))(*m)
+    na = (ctypes.c_int64 * max(1, len(n)))(*n)
+    code = lib.hsvd_plan(ctypes.byref(h), batch, ma, na, br, bc, mode, param, cap, tree, prec, dt, opts)
+    return code, h
+
+
+@pytest.mark.parametrize("kw", [
+    dict(batch=0), dict(m=(0,)), dict(n=(-3,)), dict(br=0), dict(bc=-1), dict(mode=7),
+    dict(mode=0, param=0.0), dict(mode=0, param=2.5), dict(mode=1, param=1.0), dict(mode=1, param=0.0),
+    dict(mode=2, param=1.5), dict(mode=2, param=0.0), dict(cap=0), dict(cap=257), dict(tree=5),
+    dict(prec=0, dt=1), dict(prec=1, dt=0), dict(prec=1, dt=2), dict(prec=2, dt=0), dict(prec=9),
+    dict(param=float("nan")),
+])
+def test_plan_rejects_invalid_arguments_without_a_device(lib, kw):
+    code, h = _plan_code(lib, **kw)
+    assert code == hsvd.HSVD_EINVAL
+    assert h.value is None  # out set to NULL on failure
+
+
+def test_plan_rejects_bad_options(lib):
+    o = hsvd.Options(-1, 0, 0.0, 0, 0, 0)
+    code, _ = _plan_code(lib, opts=ctypes.byref(o))
+    assert code == hsvd.HSVD_EINVAL
+    o = hsvd.Options(0, -5, 0.0, 0, 0, 0)
+    code, _ = _plan_code(lib, opts=ctypes.byref(o))
+    assert code == hsvd.HSVD_EINVAL
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.hsvd_plan(None, 1, None, None, 1, 1, 0, 1.0, 1, 0, 1, 1, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_run(None, None, None, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_run_host(None, None, None, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_status_query(None, 0, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_factors(None, 0, None, None, 0, None, None, 0, 0, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_workspace_bytes(None) == 0
+    assert lib.hsvd_launches_per_run(None) == -1
+    lib.hsvd_destroy(None)
+
+
+def test_valid_plan_without_device_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    code, h = _plan_code(lib)
+    assert code == hsvd.HSVD_ECUDA
+    assert h.value is None

@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated per precision):
+  * FP64 path: top-k sigma relative error <= 1e-10; subspace angle over
+    gap-separated leading groups <= 1e-6 rad.
+  * FP32 and BF16-mixed paths: top-k sigma relative error <= 1e-4; subspace
+    angle <= 1e-3 rad.
+  * Every path: Frobenius reconstruction error ||X - U S V^T|| / ||X|| within
+    1% of the oracle's, plus a rounding floor of 50 u of the path (an exactly
+    low-rank input makes the oracle's own error a rounding residue).
+The oracle consumes the same bytes as the GPU (BF16 inputs are rounded
+first), and uses the same rank tolerance, so rank decisions agree.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import hmat as H
+from paper_1710_02812_gb300 import hsvd
+from paper_1710_02812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": (1e-10, 1e-6, 1.1e-16), "f32": (1e-4, 1e-3, 6e-8), "bf16_mixed": (1e-4, 1e-3, 6e-8)}
+RANK_TOL = {"f64": 1e-12, "f32": 1e-5, "bf16_mixed": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def to_device(x, prec):
+    if prec == "f64":
+        return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def run_gpu(xs, br, bc, mode, param, prec, rank_cap=None, tree="col_then_row", **kw):
+    m = [x.shape[0] for x in xs]
+    n = [x.shape[1] for x in xs]
+    plan = hsvd.Plan(m, n, br, bc, mode, param, rank_cap=rank_cap, tree=tree, prec=prec, **kw)
+    dev = [to_device(x, prec) for x in xs]
+    plan.run(dev)
+    torch.cuda.synchronize()
+    outs = [plan.factors(i) for i in range(len(xs))]
+    st = plan.status()
+    return outs, st, plan
+
+
+def recon(x, u, s, v):
+    xd = np.asarray(x, dtype=np.float64)
+    nx = np.linalg.norm(xd)
+    return float(np.linalg.norm(xd - (u.astype(np.float64) * s) @ v.T.astype(np.float64)) / nx) if nx else 0.0
+
+
+def check(x, got, ref, prec, label=""):
+    u, s, v = got
+    stol, atol, eps = TOL[prec]
+    assert s.size == ref.s.size, f"{label}: rank {s.size} vs oracle {ref.s.size}"
+    if s.size == 0:
+        return
+    err = oracle.sigma_rel_err(s, ref.s)
+    assert err <= stol, f"{label}: sigma rel err {err:.3e} > {stol}"
+    au = oracle.metrics.leading_subspace_angle(u, ref.u, ref.s)
+    av = oracle.metrics.leading_subspace_angle(v, ref.v, ref.s)
+    assert au <= atol and av <= atol, f"{label}: angles U {au:.3e} V {av:.3e} > {atol}"
+    rg, ro = recon(x, u, s, v), recon(x, ref.u, ref.s, ref.v)
+    assert abs(rg - ro) <= 0.01 * ro + 50 * eps, f"{label}: recon {rg:.6e} vs oracle {ro:.6e}"
+    assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
+
+
+def oracle_run(x, br, bc, mode, param, prec, rank_cap=256, tree="col_then_row"):
+    rule = H.Rule(mode, param, rank_cap=rank_cap, rank_tol=RANK_TOL[prec])
+    return H.hmat_svd(np.asarray(x, dtype=np.float64), br, bc, rule, tree=tree)
+
+
+# ---------------------------------------------------------------- FP64
+
+def test_fp64_fixed_rank_512_parity():
+    """The 512 x 512, rank-10 + 1e-6 noise, 4 x 4 grid of 128^2, k = 10 case."""
+    x, cfg = W.fixed_rank_512()
+    (got,), st, _ = run_gpu([x], 128, 128, "fixed_k", 10, "f64")
+    ref = oracle_run(x, 128, 128, "fixed_k", 10, "f64")
+    check(x, got, ref, "f64", "fixed_rank_512")
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("m,n,br,bc,k", [
+    (700, 900, 256, 192, 12),   # ragged slabs and slices, 3 x 5 grid
+    (300, 200, 300, 200, 8),    # 1 x 1 grid: truncated SVD of the whole matrix
+    (520, 130, 40, 130, 6),     # 13 x 1 grid: row tree only, odd leaf count
+    (96, 1000, 96, 70, 6),      # 1 x 15 grid: column tree only
+    (257, 263, 64, 64, 20),     # ragged tail of 1-2 rows/cols, k' capped by block
+])
+def test_fp64_grids(m, n, br, bc, k):
+    s = 0.8 ** np.arange(min(m, n, 60))
+    x = W.planted(m, n, s, noise=1e-9, tag=m + 7 * n)
+    (got,), st, _ = run_gpu([x], br, bc, "fixed_k", k, "f64")
+    ref = oracle_run(x, br, bc, "fixed_k", k, "f64")
+    check(x, got, ref, "f64", f"{m}x{n}/{br}x{bc}")
+
+
+def test_fp64_exact_rank_recovery():
+    s = np.array([4.0, 2.5, 1.0, 0.4])
+    x, u0, s0, v0 = W.planted(333, 444, s, noise=0.0, tag=9, return_factors=True)
+    (got,), st, _ = run_gpu([x], 100, 120, "fixed_k", 8, "f64")
+    u, sg, v = got
+    assert sg.size == 4
+    np.testing.assert_allclose(sg, s, rtol=1e-10)
+    assert oracle.principal_angle(u, u0) < 1e-8 and oracle.principal_angle(v, v0) < 1e-8
+
+
+def test_fp64_row_then_col():
+    x, _ = W.fixed_rank_512()
+    x = x[:400, :300]
+    (got,), _, _ = run_gpu([x], 96, 128, "fixed_k", 10, "f64", tree="row_then_col")
+    ref = oracle_run(x, 96, 128, "fixed_k", 10, "f64", tree="row_then_col")
+    check(x, got, ref, "f64", "row_then_col")
+
+
+# ---------------------------------------------------------------- FP32
+
+@pytest.mark.parametrize("m,n,br,bc,k", [
+    (1500, 1300, 384, 320, 32),
+    (1024, 1024, 256, 256, 48),
+    (777, 2049, 200, 512, 24),
+])
+def test_fp32_exp_decay(m, n, br, bc, k):
+    x = W.exp_decay(m, n, r=min(m, n, 400), noise=1e-5, tag=m + n, dtype=np.float32)
+    (got,), st, _ = run_gpu([x], br, bc, "fixed_k", k, "f32")
+    ref = oracle_run(x, br, bc, "fixed_k", k, "f32")
+    check(x, got, ref, "f32", f"{m}x{n}")
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0
+
+
+def test_fp32_exact_rank_recovery():
+    s = np.array([3.0, 2.0, 1.5, 0.7, 0.3])
+    x, u0, s0, v0 = W.planted(600, 500, s, noise=0.0, tag=12, return_factors=True)
+    x = x.astype(np.float32)
+    (got,), st, _ = run_gpu([x], 128, 128, "fixed_k", 16, "f32")
+    u, sg, v = got
+    assert sg.size == 5
+    np.testing.assert_allclose(sg, s, rtol=1e-5)
+    assert oracle.principal_angle(u, u0) < 1e-4 and oracle.principal_angle(v, v0) < 1e-4
+
+
+def test_fp32_batch_of_uneven_matrices():
+    sizes = [(600, 450, 9), (1030, 700, 20), (300, 1200, 14), (129, 131, 5)]
+    xs = [W.ragged_matrix(m, n, r, tag=i) for i, (m, n, r) in enumerate(sizes)]
+    outs, st, _ = run_gpu(xs, 256, 256, "fixed_k", 24, "f32")
+    for x, got in zip(xs, outs):
+        ref = oracle_run(x, 256, 256, "fixed_k", 24, "f32")
+        check(x, got, ref, "f32", f"batch {x.shape}")
+
+
+def test_fp32_gamma_mode():
+    s = np.array([10.0, 7.0, 5.0, 3.0, 1.0, 0.5, 0.2, 0.05])
+    x = W.planted(800, 640, s, noise=1e-6, tag=21).astype(np.float32)
+    (got,), _, _ = run_gpu([x], 200, 160, "gamma", 0.02, "f32", rank_cap=32)
+    ref = oracle_run(x, 200, 160, "gamma", 0.02, "f32", rank_cap=32)
+    check(x, got, ref, "f32", "gamma")
+
+
+def test_fp32_energy_mode():
+    s = np.sqrt(np.array([50.0, 25.0, 12.0, 6.0, 3.0, 1.5, 0.8]))
+    x = W.planted(900, 700, s, noise=1e-7, tag=22).astype(np.float32)
+    (got,), _, _ = run_gpu([x], 300, 350, "energy", 0.97, "f32", rank_cap=16)
+    ref = oracle_run(x, 300, 350, "energy", 0.97, "f32", rank_cap=16)
+    check(x, got, ref, "f32", "energy")
+
+
+def test_fp32_zero_matrix_and_tiny_shapes():
+    (got,), st, _ = run_gpu([np.zeros((100, 80), np.float32)], 32, 32, "fixed_k", 4, "f32")
+    assert got[1].size == 0
+    x = np.array([[3.0]], dtype=np.float32)
+    (got,), _, _ = run_gpu([x], 1, 1, "fixed_k", 1, "f32")
+    np.testing.assert_allclose(got[1], [3.0], rtol=1e-6)
+    x = W.planted(3, 5, [2.0, 1.0], tag=4).astype(np.float32)
+    (got,), _, _ = run_gpu([x], 2, 2, "fixed_k", 2, "f32")
+    ref = oracle_run(x, 2, 2, "fixed_k", 2, "f32")
+    check(x, got, ref, "f32", "3x5")
+
+
+# ---------------------------------------------------------------- mixed
+
+def test_bf16_mixed_matches_oracle_on_rounded_input():
+    x32 = W.exp_decay(1024, 1536, r=300, noise=1e-5, tag=31, dtype=np.float32)
+    xb = W.bf16_round(x32)
+    (got,), st, _ = run_gpu([xb], 256, 256, "fixed_k", 32, "bf16_mixed")
+    ref = oracle_run(xb, 256, 256, "fixed_k", 32, "bf16_mixed")
+    check(xb, got, ref, "bf16_mixed", "bf16")
+
+
+# ---------------------------------------------------------------- API paths
+
+def test_run_host_equals_run_device():
+    x = W.exp_decay(900, 700, r=200, noise=1e-5, tag=41, dtype=np.float32)
+    plan = hsvd.Plan(900, 700, 256, 256, "fixed_k", 16, prec="f32", host_staging=True)
+    plan.run([to_device(x, "f32")])
+    u1, s1, v1 = plan.factors(0)
+    plan.run_host([x])
+    torch.cuda.synchronize()
+    u2, s2, v2 = plan.factors(0)
+    np.testing.assert_array_equal(s1, s2)
+    np.testing.assert_array_equal(u1, u2)
+    np.testing.assert_array_equal(v1, v2)
+
+
+def test_factors_device_matches_host():
+    x = W.exp_decay(500, 400, r=100, noise=1e-5, tag=42, dtype=np.float32)
+    plan = hsvd.Plan(500, 400, 128, 128, "fixed_k", 8, prec="f32")
+    plan.run([to_device(x, "f32")])
+    u, s, v = plan.factors(0)
+    U = torch.zeros((8, 500), dtype=torch.float32, device="cuda")
+    V = torch.zeros((8, 400), dtype=torch.float32, device="cuda")
+    S = torch.zeros(8, dtype=torch.float32, device="cuda")
+    r = plan.factors_device(U, S, V, 0)
+    torch.cuda.synchronize()
+    assert r == s.size
+    np.testing.assert_array_equal(U[:r].cpu().numpy().T, u)
+    np.testing.assert_array_equal(V[:r].cpu().numpy().T, v)
+    np.testing.assert_array_equal(S[:r].cpu().numpy(), s)
+
+
+def test_repeat_runs_are_deterministic():
+    x = W.exp_decay(700, 600, r=150, noise=1e-5, tag=43, dtype=np.float32)
+    plan = hsvd.Plan(700, 600, 160, 160, "fixed_k", 12, prec="f32")
+    xd = to_device(x, "f32")
+    plan.run([xd])
+    a = plan.factors(0)
+    plan.run([xd])
+    b = plan.factors(0)
+    for p, q in zip(a, b):
+        np.testing.assert_array_equal(p, q)
+
+
+# ---------------------------------------------------------------- status words
+
+def test_sweep_cap_reports_not_converged_without_failing():
+    x = W.exp_decay(512, 512, r=200, noise=1e-5, tag=44, dtype=np.float32)
+    (_,), st, _ = run_gpu([x], 128, 128, "fixed_k", 16, "f32", max_sweeps=1)
+    assert st["not_converged"] > 0
+
+
+def test_nonfinite_input_is_reported():
+    x = W.exp_decay(256, 256, r=64, noise=1e-5, tag=45, dtype=np.float32)
+    x[17, 33] = np.nan
+    (_,), st, _ = run_gpu([x], 64, 64, "fixed_k", 8, "f32")
+    assert st["nonfinite"] > 0
