@@ -87,7 +87,7 @@ typedef enum {
 typedef struct {
   int32_t oversample;   /* p: block sketch width k' = k + p (default p = k), capped at 256 */
   int32_t power_iters;  /* q: power steps of the block range finder; 0 = default
-                           (3 for F64, 2 otherwise), -1 = none, > 0 = that many */
+                           (6 for F64, 2 otherwise), -1 = none, > 0 = that many */
   double rank_tol;      /* relative numerical-zero level (default 1e-12 F64, 1e-5 otherwise) */
   uint64_t seed;        /* seed of the block sketch matrix (default 0x1710028) */
   int32_t max_sweeps;   /* one-sided Jacobi sweep cap (default 40) */

@@ -7,5 +7,5 @@ from .hmat import (ENERGY, FIXED_K, GAMMA, Result, Rule, Trace, block_svd,  # no
                    grid, hmat_svd, mat_merge, mat_merge_orth, merge_tree,
                    normalise_signs, recover_left, relative_error, slab_step,
                    thin_svd, tree_schedule, truncated_svd)
-from .metrics import (orthonormality_defect, principal_angle,  # noqa: F401
-                      sigma_rel_err, subspace_angles_grouped)
+from .metrics import (gap_prefix, leading_subspace_angle, orthonormality_defect,  # noqa: F401
+                      principal_angle, sigma_rel_err, subspace_angles_grouped)

@@ -87,3 +87,16 @@ def orthonormality_defect(u) -> float:
     if u.shape[1] == 0:
         return 0.0
     return float(np.max(np.abs(u.T @ u - np.eye(u.shape[1]))))
+
+
+def gap_prefix(s_true, k, rel_gap=1e-2):
+    """Largest j <= k such that s_true[j-1] is separated from s_true[j] by a
+    relative gap (j == len(s_true) counts as separated).  Singular values and
+    subspaces beyond such a gap, inside a dense cluster, are not determined
+    to better than the cluster width and are not gated."""
+    s_true = np.asarray(s_true, dtype=np.float64)
+    best = 0
+    for j in range(1, min(k, s_true.size) + 1):
+        if j == s_true.size or (s_true[j - 1] - s_true[j]) > rel_gap * s_true[j - 1]:
+            best = j
+    return best

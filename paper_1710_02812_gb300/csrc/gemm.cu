@@ -3,9 +3,9 @@
 // NN:  C = alpha [A | A2] B + beta C0   (sketch Y = B_blk Omega, power steps,
 //      Q = Y R^{-1}, the merge update U = [U1 U_o] U_E, final Y = X V_r)
 // TN:  C = alpha A^T B                  (W = B_blk^T Q, Gram matrices Y^T Y,
-//      P = U1^T U2, slab projection Z_j^T = X_j^T U_j), optionally split
-//      along K into partial tiles that a second launch sums in a fixed order
-//      (deterministic, no atomics).
+//      P = U1^T U2, slab projection Z_j^T = X_j^T U_j)
+// Both may be split along K into partial tiles that a second launch sums in
+// a fixed order (deterministic, no atomics).
 //
 // One launch serves every task of a tree level: blockIdx.x indexes a work
 // item list (task, tile row, tile column, K chunk) built at plan time.  Task
@@ -44,6 +44,11 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(const GemmTask<TA, TB, TC>* __re
   const int Kt = K1 + K2;
   const int m0 = it.mt * BM, n0 = it.nt * BN;
   if (m0 >= M || n0 >= N) return;
+  int kb = 0, ke = Kt;
+  if (tk.kchunk > 0) {
+    kb = it.kc * tk.kchunk;
+    ke = min(Kt, kb + tk.kchunk);
+  }
   const TA* A = tk.A;
   int64_t lda = tk.lda;
   if (tk.mat >= 0) {
@@ -63,12 +68,12 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(const GemmTask<TA, TB, TC>* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
 
-  for (int k0 = 0; k0 < Kt; k0 += BK) {
+  for (int k0 = kb; k0 < ke; k0 += BK) {
     for (int idx = tid; idx < BM * BK; idx += NT) {
       const int r = idx / BK, c = idx % BK;
       const int gm = m0 + r, gk = k0 + c;
       Acc v = Acc(0);
-      if (gm < M && gk < Kt) {
+      if (gm < M && gk < ke) {
         if (gk < K1)
           v = cvt<Acc>(A[(int64_t)gm * lda + gk]);
         else
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(const GemmTask<TA, TB, TC>* __re
     for (int idx = tid; idx < BK * BN; idx += NT) {
       const int r = idx / BN, c = idx % BN;
       const int gk = k0 + r, gn = n0 + c;
-      Bs[r][c] = (gk < Kt && gn < N) ? cvt<Acc>(B[(int64_t)gk * ldb + gn]) : Acc(0);
+      Bs[r][c] = (gk < ke && gn < N) ? cvt<Acc>(B[(int64_t)gk * ldb + gn]) : Acc(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -95,6 +100,14 @@ __global__ void __launch_bounds__(NT) k_gemm_nn(const GemmTask<TA, TB, TC>* __re
         for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
     }
     __syncthreads();
+  }
+  if (tk.partial) {
+    TC* P = tk.partial + ((int64_t)(it.kc * tk.mtiles + it.mt) * tk.ntiles + it.nt) * (BM * BN);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) P[(ty * 4 + i) * BN + tx * 4 + j] = acc[i][j];
+    return;
   }
   const Acc alpha = Acc(tk.alpha), beta = Acc(tk.beta);
 #pragma unroll

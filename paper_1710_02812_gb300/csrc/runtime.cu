@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -222,9 +223,10 @@ struct Builder {
       g.kchunk = 0;
       g.partial = nullptr;
       if (g.M.cap <= 0 || g.N.cap <= 0) continue;
-      if (is_tn && g.K.cap > KCHUNK) {
+      const int ktot = g.K.cap + (is_tn ? 0 : g.K2.cap);
+      if (ktot > KCHUNK) {
         g.kchunk = KCHUNK;
-        g.nkc = cdiv(g.K.cap, KCHUNK);
+        g.nkc = cdiv(ktot, KCHUNK);
         g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * TILE * TILE);
         for (int mt = 0; mt < g.mtiles; ++mt)
           for (int nt = 0; nt < g.ntiles; ++nt) red.push_back(GemmItem{(int)t, mt, nt, 0});
@@ -261,6 +263,13 @@ struct Builder {
       P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
                                return launch_gemm_nn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
                                                                 p->d_mats, s);
+                             }});
+    }
+    if (!is_tn && !red.empty()) {
+      const size_t br = P.add_blob(red);
+      const int nr = (int)red.size();
+      P.steps.push_back(Step{name + ".reduce", [p, bt, br, nr](cudaStream_t s) {
+                               return launch_gemm_reduce<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(br), nr, s);
                              }});
     }
   }
@@ -973,7 +982,7 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   P.kcap = std::min(rank_cap, base_k);
   P.kp = std::min(256, base_k + (o.oversample > 0 ? o.oversample : base_k));
   P.kp = std::max(P.kp, P.kcap);
-  P.q = o.power_iters == 0 ? (prec == HSVD_PREC_F64 ? 3 : 2) : (o.power_iters < 0 ? 0 : o.power_iters);
+  P.q = o.power_iters == 0 ? (prec == HSVD_PREC_F64 ? 6 : 2) : (o.power_iters < 0 ? 0 : o.power_iters);
   P.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
   P.rank_tol = o.rank_tol > 0 ? o.rank_tol : (prec == HSVD_PREC_F64 ? 1e-12 : 1e-5);
   P.seed = o.seed ? o.seed : 0x1710028ull;
@@ -1053,11 +1062,47 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
       if (hsvd::launch_f32_to_bf16(static_cast<const float*>(A[b]), lda[b], static_cast<__nv_bfloat16*>(P.conv[b]),
                                    P.n[b], P.m[b], P.n[b], s) != cudaSuccess)
         return HSVD_ECUDA;
-  for (auto& st : P.steps) {
-    if (st.run(s) != cudaSuccess) {
+  const bool trace = std::getenv("HSVD_TRACE") != nullptr;
+  std::vector<cudaEvent_t> ev;
+  if (trace) {
+    ev.resize(P.steps.size() + 1);
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], s);
+  }
+  for (size_t i = 0; i < P.steps.size(); ++i) {
+    if (P.steps[i].run(s) != cudaSuccess) {
       cudaGetLastError();
       return HSVD_ECUDA;
     }
+    if (trace) cudaEventRecord(ev[i + 1], s);
+  }
+  if (trace) {
+    // Per-step device time, summed by step name with the level index removed.
+    cudaEventSynchronize(ev.back());
+    std::vector<std::pair<std::string, float>> agg;
+    float total = 0.f;
+    for (size_t i = 0; i < P.steps.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      total += ms;
+      std::string key = P.steps[i].name;
+      const size_t lv = key.find(".L");
+      if (lv != std::string::npos) {
+        const size_t dot = key.find('.', lv + 1);
+        key = key.substr(0, lv) + (dot == std::string::npos ? "" : key.substr(dot));
+      }
+      bool found = false;
+      for (auto& a : agg)
+        if (a.first == key) {
+          a.second += ms;
+          found = true;
+        }
+      if (!found) agg.push_back({key, ms});
+    }
+    std::fprintf(stderr, "[hsvd trace] %zu launches, %.3f ms\n", P.steps.size(), total);
+    for (auto& a : agg) std::fprintf(stderr, "[hsvd trace] %-32s %9.3f ms %5.1f%%\n", a.first.c_str(), a.second,
+                                     100.f * a.second / (total > 0 ? total : 1.f));
+    for (auto& e : ev) cudaEventDestroy(e);
   }
   P.ran = true;
   P.last_stream = s;

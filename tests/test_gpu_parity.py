@@ -57,17 +57,24 @@ def recon(x, u, s, v):
     return float(np.linalg.norm(xd - (u.astype(np.float64) * s) @ v.T.astype(np.float64)) / nx) if nx else 0.0
 
 
-def check(x, got, ref, prec, label=""):
+def check(x, got, ref, prec, label, s_true):
+    """Gate sigma and subspaces on the leading gap-separated prefix of the
+    planted spectrum s_true (values inside a dense cluster, e.g. a noise bulk, are not
+    determined to the tolerance); the rest is checked loosely, normwise."""
     u, s, v = got
     stol, atol, eps = TOL[prec]
     assert s.size == ref.s.size, f"{label}: rank {s.size} vs oracle {ref.s.size}"
     if s.size == 0:
         return
-    err = oracle.sigma_rel_err(s, ref.s)
-    assert err <= stol, f"{label}: sigma rel err {err:.3e} > {stol}"
-    au = oracle.metrics.leading_subspace_angle(u, ref.u, ref.s)
-    av = oracle.metrics.leading_subspace_angle(v, ref.v, ref.s)
+    j = oracle.gap_prefix(s_true, s.size)
+    assert j > 0, f"{label}: no gap-separated prefix"
+    err = oracle.sigma_rel_err(s, ref.s, j)
+    assert err <= stol, f"{label}: sigma rel err {err:.3e} > {stol} over the first {j}"
+    au = oracle.leading_subspace_angle(u, ref.u, ref.s, upto=j)
+    av = oracle.leading_subspace_angle(v, ref.v, ref.s, upto=j)
     assert au <= atol and av <= atol, f"{label}: angles U {au:.3e} V {av:.3e} > {atol}"
+    normwise = float(np.max(np.abs(s - ref.s)) / ref.s[0])
+    assert normwise <= max(1e-2, stol), f"{label}: normwise sigma err {normwise:.3e}"
     rg, ro = recon(x, u, s, v), recon(x, ref.u, ref.s, ref.v)
     assert abs(rg - ro) <= 0.01 * ro + 50 * eps, f"{label}: recon {rg:.6e} vs oracle {ro:.6e}"
     assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
@@ -85,7 +92,7 @@ def test_fp64_fixed_rank_512_parity():
     x, cfg = W.fixed_rank_512()
     (got,), st, _ = run_gpu([x], 128, 128, "fixed_k", 10, "f64")
     ref = oracle_run(x, 128, 128, "fixed_k", 10, "f64")
-    check(x, got, ref, "f64", "fixed_rank_512")
+    check(x, got, ref, "f64", "fixed_rank_512", s_true=10.0 ** (-np.arange(10) / 3.0))
     assert st["not_converged"] == 0 and st["nonfinite"] == 0
 
 
@@ -101,7 +108,7 @@ def test_fp64_grids(m, n, br, bc, k):
     x = W.planted(m, n, s, noise=1e-9, tag=m + 7 * n)
     (got,), st, _ = run_gpu([x], br, bc, "fixed_k", k, "f64")
     ref = oracle_run(x, br, bc, "fixed_k", k, "f64")
-    check(x, got, ref, "f64", f"{m}x{n}/{br}x{bc}")
+    check(x, got, ref, "f64", f"{m}x{n}/{br}x{bc}", s_true=s)
 
 
 def test_fp64_exact_rank_recovery():
@@ -119,7 +126,7 @@ def test_fp64_row_then_col():
     x = x[:400, :300]
     (got,), _, _ = run_gpu([x], 96, 128, "fixed_k", 10, "f64", tree="row_then_col")
     ref = oracle_run(x, 96, 128, "fixed_k", 10, "f64", tree="row_then_col")
-    check(x, got, ref, "f64", "row_then_col")
+    check(x, got, ref, "f64", "row_then_col", s_true=np.linalg.svd(x, compute_uv=False)[:10])
 
 
 # ---------------------------------------------------------------- FP32
@@ -133,7 +140,7 @@ def test_fp32_exp_decay(m, n, br, bc, k):
     x = W.exp_decay(m, n, r=min(m, n, 400), noise=1e-5, tag=m + n, dtype=np.float32)
     (got,), st, _ = run_gpu([x], br, bc, "fixed_k", k, "f32")
     ref = oracle_run(x, br, bc, "fixed_k", k, "f32")
-    check(x, got, ref, "f32", f"{m}x{n}")
+    check(x, got, ref, "f32", f"{m}x{n}", s_true=np.exp(-np.arange(min(m, n, 400)) / 20.0))
     assert st["not_converged"] == 0 and st["nonfinite"] == 0
 
 
@@ -152,9 +159,10 @@ def test_fp32_batch_of_uneven_matrices():
     sizes = [(600, 450, 9), (1030, 700, 20), (300, 1200, 14), (129, 131, 5)]
     xs = [W.ragged_matrix(m, n, r, tag=i) for i, (m, n, r) in enumerate(sizes)]
     outs, st, _ = run_gpu(xs, 256, 256, "fixed_k", 24, "f32")
-    for x, got in zip(xs, outs):
+    for (m, n, r), x, got in zip(sizes, xs, outs):
         ref = oracle_run(x, 256, 256, "fixed_k", 24, "f32")
-        check(x, got, ref, "f32", f"batch {x.shape}")
+        # k = 24 exceeds every planted rank: only the planted part is gated
+        check(x, got, ref, "f32", f"batch {x.shape}", s_true=np.exp(-np.arange(r) / r) / r)
 
 
 def test_fp32_gamma_mode():
@@ -162,7 +170,7 @@ def test_fp32_gamma_mode():
     x = W.planted(800, 640, s, noise=1e-6, tag=21).astype(np.float32)
     (got,), _, _ = run_gpu([x], 200, 160, "gamma", 0.02, "f32", rank_cap=32)
     ref = oracle_run(x, 200, 160, "gamma", 0.02, "f32", rank_cap=32)
-    check(x, got, ref, "f32", "gamma")
+    check(x, got, ref, "f32", "gamma", s_true=s)
 
 
 def test_fp32_energy_mode():
@@ -170,7 +178,7 @@ def test_fp32_energy_mode():
     x = W.planted(900, 700, s, noise=1e-7, tag=22).astype(np.float32)
     (got,), _, _ = run_gpu([x], 300, 350, "energy", 0.97, "f32", rank_cap=16)
     ref = oracle_run(x, 300, 350, "energy", 0.97, "f32", rank_cap=16)
-    check(x, got, ref, "f32", "energy")
+    check(x, got, ref, "f32", "energy", s_true=s)
 
 
 def test_fp32_zero_matrix_and_tiny_shapes():
@@ -182,7 +190,7 @@ def test_fp32_zero_matrix_and_tiny_shapes():
     x = W.planted(3, 5, [2.0, 1.0], tag=4).astype(np.float32)
     (got,), _, _ = run_gpu([x], 2, 2, "fixed_k", 2, "f32")
     ref = oracle_run(x, 2, 2, "fixed_k", 2, "f32")
-    check(x, got, ref, "f32", "3x5")
+    check(x, got, ref, "f32", "3x5", s_true=[2.0, 1.0])
 
 
 # ---------------------------------------------------------------- mixed
@@ -192,7 +200,7 @@ def test_bf16_mixed_matches_oracle_on_rounded_input():
     xb = W.bf16_round(x32)
     (got,), st, _ = run_gpu([xb], 256, 256, "fixed_k", 32, "bf16_mixed")
     ref = oracle_run(xb, 256, 256, "fixed_k", 32, "bf16_mixed")
-    check(xb, got, ref, "bf16_mixed", "bf16")
+    check(xb, got, ref, "bf16_mixed", "bf16", s_true=np.exp(-np.arange(300) / 20.0))
 
 
 # ---------------------------------------------------------------- API paths
