@@ -101,6 +101,8 @@ typedef struct {
   int32_t nonfinite;      /* cores that saw a NaN / Inf */
   int32_t min_rank;       /* smallest final rank over the batch */
   int32_t max_rank;       /* largest final rank over the batch */
+  int32_t jacobi_sweeps;  /* one-sided Jacobi sweeps summed over all cores */
+  int32_t jacobi_cores;   /* number of Jacobi cores solved */
 } hsvd_report;
 
 typedef struct hsvd_plan_s* hsvd_plan_t;
@@ -167,6 +169,35 @@ int64_t hsvd_workspace_bytes(hsvd_plan_t plan);
 /* hsvd_launches_per_run -- number of kernel launches one hsvd_run enqueues
  * (host query; -1 for NULL). */
 int32_t hsvd_launches_per_run(hsvd_plan_t plan);
+
+/* ---- instrumentation (no counterpart in the paper) ----
+ * Every run enqueues the same list of kernel launches ("steps").  These
+ * host calls describe the steps and, when timing is on, report the device
+ * time of each, measured with CUDA events recorded on the run's stream
+ * between consecutive launches. */
+
+/* hsvd_step_count -- number of steps of one run (-1 for NULL). */
+int32_t hsvd_step_count(hsvd_plan_t plan);
+
+/* hsvd_step_info -- metadata of step i: its name (NUL-terminated, truncated
+ * to name_len), kind (1 GEMM NN, 2 GEMM TN, 3 split-K reduction, 4
+ * CholeskyQR factor/inverse, 5 Jacobi core SVD, 6 block energy, 7 sign
+ * normalisation), number of tasks, the core dimension or the column count,
+ * and the algorithmic flops and bytes of the launch (GEMMs: 2MNK and one
+ * read of every operand plus one write of the result; Jacobi: 22 n^3 per
+ * n x n core, the paper's count for the merge core in Section 3.1).  Any
+ * output pointer may be NULL.  EINVAL for a bad index. */
+hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* kind,
+                           int32_t* tasks, int32_t* dim, double* flops, double* bytes);
+
+/* hsvd_set_timing -- on != 0: record events around every step of the
+ * following runs; resets the accumulated times. */
+hsvd_status hsvd_set_timing(hsvd_plan_t plan, int32_t on);
+
+/* hsvd_step_times -- synchronise on the timed runs enqueued so far and
+ * write the summed device time (ms) of each step into ms[0..n) and the
+ * number of timed runs into *runs (either may be NULL). */
+hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* runs);
 
 /* hsvd_destroy -- free everything the plan owns; NULL is accepted. */
 void hsvd_destroy(hsvd_plan_t plan);

@@ -39,7 +39,9 @@ struct DevStatus {
   int not_converged;
   int chol_dropped;
   int nonfinite;
-  int pad;
+  int sweeps;  // Jacobi sweeps summed over all cores
+  int cores;   // Jacobi cores solved
+  int pad[3];
 };
 
 // ---------------------------------------------------------------- GEMM tasks

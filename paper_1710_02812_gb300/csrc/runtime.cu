@@ -39,6 +39,11 @@ struct Blob {
 struct Step {
   std::string name;
   std::function<cudaError_t(cudaStream_t)> run;
+  int kind = 0;   // hsvd_step_kind
+  int tasks = 0;  // tasks (blocks / merges / slabs / matrices) in the launch
+  int dim = 0;    // core dimension (Jacobi, Cholesky) or columns (GEMMs)
+  double flops = 0;  // algorithmic flops of the launch (see hsvd_step_info)
+  double bytes = 0;  // algorithmic bytes of the launch
 };
 
 struct ProblemOut {
@@ -85,6 +90,10 @@ struct PlanImpl {
   bool ran = false;
   cudaStream_t last_stream = nullptr;
   int launches_per_run = 0;
+  bool timing = false;  // record an event after every step of every run
+  std::vector<std::vector<cudaEvent_t>> pending, pool;  // event sets of timed runs
+  std::vector<double> step_ms;  // per-step device time summed over collected runs
+  int timed_runs = 0;
   int dev = 0;
 
   ~PlanImpl() {
@@ -96,6 +105,26 @@ struct PlanImpl {
     if (mats_done) cudaEventDestroy(mats_done);
     for (void* p : conv) cudaFree(p);
     for (void* p : staging) cudaFree(p);
+    for (auto& v : pending)
+      for (auto e : v) cudaEventDestroy(e);
+    for (auto& v : pool)
+      for (auto e : v) cudaEventDestroy(e);
+  }
+  // Fold the events of every pending timed run into step_ms (synchronises
+  // on the last event of each).
+  void collect_timing() {
+    if (step_ms.size() != steps.size()) step_ms.assign(steps.size(), 0.0);
+    for (auto& v : pending) {
+      cudaEventSynchronize(v.back());
+      for (size_t i = 0; i + 1 < v.size(); ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, v[i], v[i + 1]);
+        step_ms[i] += ms;
+      }
+      ++timed_runs;
+      pool.push_back(std::move(v));
+    }
+    pending.clear();
   }
 
   template <class X>
@@ -237,12 +266,40 @@ struct Builder {
     }
   }
 
+  void tag(int kind, int tasks, int dim, double flops, double bytes) {
+    Step& st = P.steps.back();
+    st.kind = kind;
+    st.tasks = tasks;
+    st.dim = dim;
+    st.flops = flops;
+    st.bytes = bytes;
+  }
+
+  // Algorithmic work of a GEMM launch from its (capped) extents: 2 M N K
+  // flops; A, B read once and C written once.
+  template <class G>
+  static void gemm_work(const std::vector<G>& tasks, bool is_tn, double& flops, double& bytes, int& ncols) {
+    using TAx = typename TaOf<G>::type;
+    flops = bytes = 0;
+    ncols = 0;
+    for (const auto& g : tasks) {
+      const double M = g.M.cap, N = g.N.cap, K = g.K.cap + (is_tn ? 0 : g.K2.cap);
+      flops += 2.0 * M * N * K;
+      bytes += M * K * sizeof(TAx) + K * N * sizeof(T) + M * N * sizeof(T);
+      ncols = std::max(ncols, g.N.cap);
+    }
+  }
+
   template <class G>
   void emit_gemm(const std::string& name, std::vector<G> tasks, bool is_tn) {
     if (tasks.empty()) return;
     std::vector<GemmItem> items, red;
     finish_items(tasks, is_tn, items, red);
     if (items.empty()) return;
+    double gfl, gby;
+    int gcols;
+    gemm_work(tasks, is_tn, gfl, gby, gcols);
+    const int ntask = (int)tasks.size();
     PlanImpl* p = &P;
     const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
     const int ni = (int)items.size();
@@ -252,18 +309,21 @@ struct Builder {
                                return launch_gemm_tn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
                                                                 p->d_mats, s);
                              }});
+      tag(2, ntask, gcols, gfl, gby);
       if (!red.empty()) {
         const size_t br = P.add_blob(red);
         const int nr = (int)red.size();
         P.steps.push_back(Step{name + ".reduce", [p, bt, br, nr](cudaStream_t s) {
                                  return launch_gemm_reduce<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(br), nr, s);
                                }});
+        tag(3, ntask, gcols, 0, 0);
       }
     } else {
       P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
                                return launch_gemm_nn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
                                                                 p->d_mats, s);
                              }});
+      tag(1, ntask, gcols, gfl, gby);
     }
     if (!is_tn && !red.empty()) {
       const size_t br = P.add_blob(red);
@@ -271,6 +331,7 @@ struct Builder {
       P.steps.push_back(Step{name + ".reduce", [p, bt, br, nr](cudaStream_t s) {
                                return launch_gemm_reduce<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(br), nr, s);
                              }});
+      tag(3, ntask, gcols, 0, 0);
     }
   }
 
@@ -339,6 +400,15 @@ struct Builder {
     P.steps.push_back(Step{name, [p, bt, nt, kcapl, tau](cudaStream_t s) {
                              return launch_chol<T>(p->table<CholTask<T>>(bt), nt, kcapl, p->d_status, tau, s);
                            }});
+    {
+      double fl = 0, by = 0;
+      for (const auto& t : tasks) {
+        const double k = t.k.cap;
+        fl += k * k * k;  // factor k^3/3, inverse k^3/3, product k^3/3
+        by += 3.0 * k * k * sizeof(T);
+      }
+      tag(4, nt, kcapl, fl, by);
+    }
   }
 
   void emit_jacobi(const std::string& name, std::vector<JacobiTask<T>> tasks, int nrcap, int nccap, bool want_v,
@@ -355,6 +425,17 @@ struct Builder {
                              return launch_jacobi<T>(p->table<JacobiTask<T>>(bt), nt, nrcap, nccap, want_v, tp,
                                                      p->d_status, s);
                            }});
+    {
+      // Algorithmic flops of an SVD of an n x n core: 22 n^3, the count the
+      // paper uses for the merge core (Section 3.1: 176 k^3 for 2k x 2k).
+      double fl = 0, by = 0;
+      for (const auto& t : tasks) {
+        const double nn = (t.load == 1) ? (double)(t.k1.cap + t.k2.cap) : (double)std::max(t.nr.cap, t.nc.cap);
+        fl += 22.0 * nn * nn * nn;
+        by += 2.0 * nn * nn * sizeof(T);
+      }
+      tag(5, nt, std::max(nrcap, nccap), fl, by);
+    }
   }
 
   JacobiTask<T> jblank() const {
@@ -646,6 +727,9 @@ struct Builder {
       P.steps.push_back(Step{"block.energy", [p, bt, nt](cudaStream_t s) {
                                return launch_block_energy<TA, T>(p->table<EnergyTask>(bt), nt, p->d_mats, s);
                              }});
+      double by = 0;
+      for (auto& e : et) by += (double)e.h * e.w * sizeof(TA);
+      tag(6, nt, 0, 2.0 * by / sizeof(TA), by);
     }
     {
       std::vector<InputOp> ops;
@@ -827,6 +911,7 @@ struct Builder {
         P.steps.push_back(Step{"final.signs", [su, sv, mu, mv, rk, kc](cudaStream_t s) {
                                  return launch_sign_normalise<T>(su, kc, mu, sv, kc, mv, rk, kc, s);
                                }});
+        tag(7, 1, kc, 0, (double)(mu + mv) * kc * sizeof(T));
       }
     }
   }
@@ -1063,27 +1148,38 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
                                    P.n[b], P.m[b], P.n[b], s) != cudaSuccess)
         return HSVD_ECUDA;
   const bool trace = std::getenv("HSVD_TRACE") != nullptr;
+  const bool timed = P.timing || trace;
   std::vector<cudaEvent_t> ev;
-  if (trace) {
-    ev.resize(P.steps.size() + 1);
-    for (auto& e : ev) cudaEventCreate(&e);
+  if (timed) {
+    if (!P.pool.empty()) {
+      ev = std::move(P.pool.back());
+      P.pool.pop_back();
+    } else {
+      ev.resize(P.steps.size() + 1);
+      for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return HSVD_ECUDA;
+    }
     cudaEventRecord(ev[0], s);
   }
   for (size_t i = 0; i < P.steps.size(); ++i) {
     if (P.steps[i].run(s) != cudaSuccess) {
       cudaGetLastError();
+      if (timed) P.pool.push_back(std::move(ev));
       return HSVD_ECUDA;
     }
-    if (trace) cudaEventRecord(ev[i + 1], s);
+    if (timed) cudaEventRecord(ev[i + 1], s);
   }
+  if (timed) P.pending.push_back(std::move(ev));
   if (trace) {
-    // Per-step device time, summed by step name with the level index removed.
-    cudaEventSynchronize(ev.back());
-    std::vector<std::pair<std::string, float>> agg;
-    float total = 0.f;
+    // Per-step device time of this run, summed by step name without the
+    // tree level, printed to stderr.
+    std::vector<double> before = P.step_ms;
+    const int runs_before = P.timed_runs;
+    P.collect_timing();
+    std::vector<std::pair<std::string, double>> agg;
+    double total = 0;
     for (size_t i = 0; i < P.steps.size(); ++i) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      const double ms = P.step_ms[i] - (i < before.size() ? before[i] : 0.0);
       total += ms;
       std::string key = P.steps[i].name;
       const size_t lv = key.find(".L");
@@ -1099,10 +1195,11 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
         }
       if (!found) agg.push_back({key, ms});
     }
-    std::fprintf(stderr, "[hsvd trace] %zu launches, %.3f ms\n", P.steps.size(), total);
-    for (auto& a : agg) std::fprintf(stderr, "[hsvd trace] %-32s %9.3f ms %5.1f%%\n", a.first.c_str(), a.second,
-                                     100.f * a.second / (total > 0 ? total : 1.f));
-    for (auto& e : ev) cudaEventDestroy(e);
+    std::fprintf(stderr, "[hsvd trace] %zu launches, %.3f ms (timed runs %d)\n", P.steps.size(), total,
+                 P.timed_runs - runs_before);
+    for (auto& a : agg)
+      std::fprintf(stderr, "[hsvd trace] %-32s %9.3f ms %5.1f%%\n", a.first.c_str(), a.second,
+                   100.0 * a.second / (total > 0 ? total : 1.0));
   }
   P.ran = true;
   P.last_stream = s;
@@ -1148,6 +1245,8 @@ hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r) {
   r->not_converged = ds.not_converged;
   r->chol_dropped = ds.chol_dropped;
   r->nonfinite = ds.nonfinite;
+  r->jacobi_sweeps = ds.sweeps;
+  r->jacobi_cores = ds.cores;
   r->min_rank = 0;
   r->max_rank = 0;
   if (P.ran) {
@@ -1248,6 +1347,49 @@ int32_t hsvd_launches_per_run(hsvd_plan_t plan) {
   if (!plan) return -1;
   const PlanImpl& P = plan->impl;
   return P.launches_per_run + (P.conv.empty() ? 0 : P.batch);
+}
+
+int32_t hsvd_step_count(hsvd_plan_t plan) {
+  if (!plan) return -1;
+  return (int32_t)plan->impl.steps.size();
+}
+
+hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* kind,
+                           int32_t* tasks, int32_t* dim, double* flops, double* bytes) {
+  if (!plan) return HSVD_EINVAL;
+  const PlanImpl& P = plan->impl;
+  if (i < 0 || i >= (int32_t)P.steps.size()) return HSVD_EINVAL;
+  const auto& st = P.steps[i];
+  if (name && name_len > 0) {
+    std::strncpy(name, st.name.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (kind) *kind = st.kind;
+  if (tasks) *tasks = st.tasks;
+  if (dim) *dim = st.dim;
+  if (flops) *flops = st.flops;
+  if (bytes) *bytes = st.bytes;
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_set_timing(hsvd_plan_t plan, int32_t on) {
+  if (!plan) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  P.collect_timing();
+  P.timing = on != 0;
+  P.step_ms.assign(P.steps.size(), 0.0);
+  P.timed_runs = 0;
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* runs) {
+  if (!plan) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  P.collect_timing();
+  if (ms)
+    for (int32_t i = 0; i < n && i < (int32_t)P.step_ms.size(); ++i) ms[i] = P.step_ms[i];
+  if (runs) *runs = P.timed_runs;
+  return HSVD_OK;
 }
 
 void hsvd_destroy(hsvd_plan_t plan) { delete plan; }

@@ -42,20 +42,23 @@ __device__ __forceinline__ T dsqrt(T x) {
 // the upper triangle (incl. diagonal) holds the trailing Gram entries and
 // finally the unit-row factor U = D L^T; the strictly lower triangle holds
 // the unit lower inverse L^{-1}.  R = D^{-1/2} U S^{-1}, R^{-1} = S L^{-T} D^{-1/2}.
+// Thread (ty, tx) of the 16 x 16 CTA owns the entries (i, c) with
+// i = ty mod 16, c = tx mod 16, so no index division is needed.
 template <class T>
 __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ tasks, int kcap,
                                               DevStatus* __restrict__ st, T tau, int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T sc[256];
   __shared__ T dpv[256];
+  __shared__ int bad;
   const CholTask<T>& tk = tasks[blockIdx.x];
   const int k = eff(tk.k);
   if (k <= 0) return;
   T* M = use_smem ? reinterpret_cast<T*>(smem_raw) : tk.work;
   const int ld = k;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int ty = tid >> 4, tx = tid & 15;
 
-  __shared__ int bad;
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int j = tid; j < k; j += nt) {
@@ -65,17 +68,16 @@ __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ ta
   }
   __syncthreads();
   if (tid == 0 && bad && st) atomicAdd(&st->nonfinite, 1);
-  for (int e = tid; e < k * k; e += nt) {
-    const int i = e / k, j = e % k;
-    M[i * ld + j] = (j >= i) ? tk.G[(int64_t)i * tk.ldg + j] * sc[i] * sc[j] : T(0);
-  }
+  for (int i = ty; i < k; i += 16)
+    for (int j = tx; j < k; j += 16)
+      M[i * ld + j] = (j >= i) ? tk.G[(int64_t)i * tk.ldg + j] * sc[i] * sc[j] : T(0);
   __syncthreads();
 
   int ndrop = 0;
   for (int j = 0; j < k; ++j) {
     const T d = M[j * ld + j];
     const bool drop = !(sc[j] > T(0)) || !(d > tau);
-    __syncthreads();  // every thread has read d before row j+1.. are touched
+    __syncthreads();
     if (drop) {
       if (tid == 0) dpv[j] = T(0);
       ++ndrop;
@@ -83,59 +85,52 @@ __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ ta
     }
     if (tid == 0) dpv[j] = d;
     const T dinv = T(1) / d;
-    const int rows = k - j - 1;
-    for (int e = tid; e < rows * k; e += nt) {
-      const int i = j + 1 + e / k;
-      const int c = e % k;
-      const T f = M[j * ld + i] * dinv;
-      if (c >= i) {
-        M[i * ld + c] -= f * M[j * ld + c];
-      } else if (c < j) {
-        M[i * ld + c] -= f * M[j * ld + c];
-      } else if (c == j) {
-        M[i * ld + j] = -f;
-      }
+    const T* rowj = M + j * ld;
+    int i0 = j + 1 + ((ty - (j + 1)) & 15);
+    for (int i = i0; i < k; i += 16) {
+      T* rowi = M + i * ld;
+      const T f = rowj[i] * dinv;
+      for (int c = tx; c < j; c += 16) rowi[c] -= f * rowj[c];
+      if ((j & 15) == tx) rowi[j] = -f;
+      for (int c = i + ((tx - i) & 15); c < k; c += 16) rowi[c] -= f * rowj[c];
     }
     __syncthreads();
   }
-  __syncthreads();
   if (tid == 0 && ndrop > 0 && st) atomicAdd(&st->chol_dropped, ndrop);
 
   // R^{-1}[l][j] = s_l * Linv[j][l] / sqrt(d_j)  (l <= j, Linv[j][j] = 1)
   if (tk.Rinv) {
-    for (int e = tid; e < k * k; e += nt) {
-      const int l = e / k, j = e % k;
-      T v = T(0);
-      if (l <= j && dpv[j] > T(0)) {
-        const T lij = (l == j) ? T(1) : M[j * ld + l];
-        v = sc[l] * lij / dsqrt(dpv[j]);
+    for (int l = ty; l < k; l += 16)
+      for (int j = tx; j < k; j += 16) {
+        T v = T(0);
+        if (l <= j && dpv[j] > T(0)) {
+          const T lij = (l == j) ? T(1) : M[j * ld + l];
+          v = sc[l] * lij / dsqrt(dpv[j]);
+        }
+        tk.Rinv[(int64_t)l * tk.ldri + j] = v;
       }
-      tk.Rinv[(int64_t)l * tk.ldri + j] = v;
-    }
   }
   __syncthreads();
   // R[j][c] = M[j][c] / sqrt(d_j) / s_c  (c >= j), in place in the upper part.
-  for (int e = tid; e < k * k; e += nt) {
-    const int j = e / k, c = e % k;
-    T v = T(0);
-    if (c >= j && dpv[j] > T(0) && sc[c] > T(0)) v = M[j * ld + c] / dsqrt(dpv[j]) / sc[c];
-    M[j * ld + c] = v;
-  }
+  for (int j = ty; j < k; j += 16)
+    for (int c = tx; c < k; c += 16) {
+      T v = T(0);
+      if (c >= j && dpv[j] > T(0) && sc[c] > T(0)) v = M[j * ld + c] / dsqrt(dpv[j]) / sc[c];
+      M[j * ld + c] = v;
+    }
   __syncthreads();
   if (!tk.R) return;
   if (tk.Rprev) {
-    for (int e = tid; e < k * k; e += nt) {
-      const int i = e / k, j = e % k;
-      T s = T(0);
-      if (j >= i)
-        for (int l = i; l <= j; ++l) s += M[i * ld + l] * tk.Rprev[(int64_t)l * tk.ldrp + j];
-      tk.R[(int64_t)i * tk.ldr + j] = s;
-    }
+    for (int i = ty; i < k; i += 16)
+      for (int j = tx; j < k; j += 16) {
+        T s = T(0);
+        if (j >= i)
+          for (int l = i; l <= j; ++l) s += M[i * ld + l] * tk.Rprev[(int64_t)l * tk.ldrp + j];
+        tk.R[(int64_t)i * tk.ldr + j] = s;
+      }
   } else {
-    for (int e = tid; e < k * k; e += nt) {
-      const int i = e / k, j = e % k;
-      tk.R[(int64_t)i * tk.ldr + j] = M[i * ld + j];
-    }
+    for (int i = ty; i < k; i += 16)
+      for (int j = tx; j < k; j += 16) tk.R[(int64_t)i * tk.ldr + j] = M[i * ld + j];
   }
 }
 
@@ -144,29 +139,108 @@ __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ ta
 // pairs (r+s, r-s) mod (n-1).  Each unordered pair appears once per sweep and
 // the pairs of one round are disjoint.
 __host__ __device__ __forceinline__ void rr_pair(int n, int r, int s, int& p, int& q) {
-  const int m = n - 1;
+  const int m = n - 1;  // 0 <= r < m, 0 <= s < n/2, so one conditional wrap suffices
   if (s == 0) {
     p = r;
     q = m;
   } else {
-    p = (r + s) % m;
-    q = (r - s + m) % m;
+    p = r + s;
+    if (p >= m) p -= m;
+    q = r - s;
+    if (q < 0) q += m;
   }
 }
 
-template <class T>
-__device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
-  for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
-  return v;
+// Reciprocal square root refined by one Newton step (float: hardware
+// estimate + Newton gives ~1 ulp; double: library rsqrt).
+__device__ __forceinline__ float rsq(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x, r * r, 1.5f);
+}
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+// Leading dimension of the column-major working copy: rows rounded up to the
+// bank period plus a quarter period, so the columns handled by the groups
+// of one warp start in different banks.
+__host__ __device__ __forceinline__ int jacobi_ld(int nr, int elem) {
+  const int period = elem == 8 ? 16 : 32;
+  return ((nr + period - 1) / period) * period + period / 4;
 }
 
-template <class T, bool WANT_V>
-__global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict__ tasks, int nrcap, int nccap,
-                                                TruncParams tp, DevStatus* __restrict__ st, int use_smem) {
+// Householder QR of the n x n column-major matrix A (ld lda) in shared or
+// global memory, overwritten by R^T (lower triangular); Q is not formed.
+// Each step: the norm of column j below the diagonal (one warp), then every
+// trailing column c gets A[j:, c] -= tau (v^T A[j:, c]) v, one warp per column.
+template <class T>
+__device__ void householder_r_transpose(T* A, int lda, int n, T* scratch) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  T* v = scratch;  // v[0..n), plus tau at v[n]
+  for (int j = 0; j < n - 1; ++j) {
+    T* x = A + (int64_t)j * lda;
+    if (warp == 0) {
+      T s = T(0);
+      for (int i = j + 1 + lane; i < n; i += 32) s += x[i] * x[i];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      const T x0 = x[j];
+      const T alpha = dsqrt(s + x0 * x0);
+      T tau = T(0), beta = x0, scale = T(0);
+      if (s > T(0)) {
+        beta = x0 >= T(0) ? -alpha : alpha;
+        tau = (beta - x0) / beta;
+        scale = T(1) / (x0 - beta);
+      }
+      for (int i = j + 1 + lane; i < n; i += 32) v[i] = x[i] * scale;
+      if (lane == 0) {
+        v[j] = T(1);
+        v[n] = tau;
+        x[j] = beta;
+      }
+    }
+    __syncthreads();
+    const T tau = v[n];
+    if (tau != T(0)) {
+      for (int c = j + 1 + warp; c < n; c += nwarps) {
+        T* y = A + (int64_t)c * lda;
+        T w = T(0);
+        for (int i = j + lane; i < n; i += 32) w += v[i] * y[i];
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        w *= tau;
+        for (int i = j + lane; i < n; i += 32) y[i] -= w * v[i];
+      }
+    }
+    __syncthreads();
+  }
+  // R is the upper triangle; write R^T in place (lower triangle) and zero the rest.
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e % n, c = e / n;  // element (i, c), column-major
+    if (i < c) {
+      const T r = A[(int64_t)c * lda + i];  // R[i][c]
+      A[(int64_t)i * lda + c] = r;          // R^T[c][i]
+      A[(int64_t)c * lda + i] = T(0);
+    }
+  }
+  __syncthreads();
+}
+
+// All n/2 column pairs of a round are processed at once, G lanes per pair,
+// each lane holding at most RMAX rows of the pair in registers.
+template <class T, int RMAX>
+struct JacobiOcc {
+  // two CTAs per SM when the row registers fit in 64 per thread
+  static constexpr int value = (sizeof(T) * RMAX <= 64) ? 2 : 1;
+};
+
+template <class T, bool WANT_V, int RMAX>
+__global__ void __launch_bounds__(512, JacobiOcc<T, RMAX>::value) k_jacobi(const JacobiTask<T>* __restrict__ tasks, int nrcap, int nccap,
+                                                int G, TruncParams tp, DevStatus* __restrict__ st, int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T sig_s[512];
   __shared__ int perm[512];
   __shared__ int rank_s;
+  __shared__ T hh_scratch[520];
   const JacobiTask<T>& tk = tasks[blockIdx.x];
   int nr, nc, k1 = 0, k2 = 0;
   if (tk.load == 1) {
@@ -179,44 +253,61 @@ __global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict_
   }
   const int n = nc + (nc & 1);
   const int ncc = nccap + (nccap & 1);
+  // rows are zero-padded to G * RMAX so the sweep loops need no bounds checks
+  const int rows_pad = G * RMAX;
+  const int ldm = jacobi_ld(rows_pad, (int)sizeof(T));
+  const int ldmcap = ldm;
+  const int ldv = jacobi_ld(ncc, (int)sizeof(T));
   T* Mw = use_smem ? reinterpret_cast<T*>(smem_raw) : tk.work;
-  T* Vw = WANT_V ? (Mw + (int64_t)nrcap * ncc) : nullptr;
-  const int ldm = nr > 0 ? nr : 1;
+  T* Vw = WANT_V ? (Mw + (int64_t)ldmcap * ncc) : nullptr;
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  // ---- load (column-major working copy)
-  for (int e = tid; e < nr * n; e += nt) {
-    const int i = e % nr, j = e / nr;
+  // ---- load (column-major working copy).  The merge core is loaded as
+  // E^T and replaced by R^T from a Householder QR E^T = Q R: E = R^T Q^T has
+  // the left singular vectors and singular values of R^T, and one-sided
+  // Jacobi converges in far fewer sweeps on R^T than on E.
+  for (int e = tid; e < rows_pad * n; e += nt) {
+    const int i = e % rows_pad, j = e / rows_pad;
     T v = T(0);
-    if (j < nc) {
+    if (j < nc && i < nr) {
       if (tk.load == 0) {
         v = tk.src[(int64_t)i * tk.rs + (int64_t)j * tk.cs];
-      } else if (i < k1) {
-        if (j < k1)
-          v = (i == j) ? tk.s1[i] : T(0);
-        else {
-          T p = tk.P[(int64_t)i * tk.ldp + (j - k1)];
-          if (tk.P2) p += tk.P2[(int64_t)i * tk.ldp + (j - k1)];
-          v = p * tk.s2[j - k1];
+      } else {
+        const int ei = j, ej = i;  // element (i, j) of E^T is E[j][i]
+        if (ei < k1) {
+          if (ej < k1)
+            v = (ei == ej) ? tk.s1[ei] : T(0);
+          else {
+            T p = tk.P[(int64_t)ei * tk.ldp + (ej - k1)];
+            if (tk.P2) p += tk.P2[(int64_t)ei * tk.ldp + (ej - k1)];
+            v = p * tk.s2[ej - k1];
+          }
+        } else if (ej >= k1) {
+          v = tk.R[(int64_t)(ei - k1) * tk.ldr + (ej - k1)] * tk.s2[ej - k1];
         }
-      } else if (j >= k1) {
-        v = tk.R[(int64_t)(i - k1) * tk.ldr + (j - k1)] * tk.s2[j - k1];
       }
     }
     Mw[(int64_t)j * ldm + i] = v;
   }
+  if (tk.load == 1 && nr > 1) {
+    __syncthreads();
+    householder_r_transpose<T>(Mw, ldm, nr, hh_scratch);
+  }
   if (WANT_V)
-    for (int e = tid; e < n * n; e += nt) Vw[e] = ((e / n) == (e % n)) ? T(1) : T(0);
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e % n, j = e / n;
+      Vw[(int64_t)j * ldv + i] = (i == j) ? T(1) : T(0);
+    }
   __syncthreads();
 
   // ---- sweeps
-  const int G = nr >= 128 ? 32 : (nr >= 64 ? 16 : (nr >= 24 ? 8 : 4));
   const int ngroups = nt / G;
   const int gid = tid / G, lane = tid % G;
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) / G * G));
-  const T tol = T(4.0 * Eps<T>::v * sqrt((double)(nr > 1 ? nr : 1)));
-  int sweep = 0;
+  const double told = 4.0 * Eps<T>::v * sqrt((double)(nr > 1 ? nr : 1));
+  const T tol2 = T(told * told);
   bool converged = (n <= 1);
+  int sweep = 0;
   for (; sweep < tp.max_sweeps && !converged; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < n - 1; ++r) {
@@ -224,43 +315,59 @@ __global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict_
         int p, q;
         rr_pair(n, r, slot, p, q);
         if (p >= nc || q >= nc) continue;
-        T* x = Mw + (int64_t)p * ldm;
-        T* y = Mw + (int64_t)q * ldm;
-        T a = T(0), b = T(0), c = T(0);
-        for (int i = lane; i < nr; i += G) {
-          const T xi = x[i], yi = y[i];
-          a += xi * xi;
-          b += yi * yi;
-          c += xi * yi;
+        T* x = Mw + p * ldm + lane;
+        T* y = Mw + q * ldm + lane;
+        T xr[RMAX], yr[RMAX];
+        T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0), c0 = T(0), c1 = T(0);
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+          const T xv = x[t * G], yv = y[t * G];
+          xr[t] = xv;
+          yr[t] = yv;
+          if (t & 1) {
+            a1 = fma(xv, xv, a1);
+            b1 = fma(yv, yv, b1);
+            c1 = fma(xv, yv, c1);
+          } else {
+            a0 = fma(xv, xv, a0);
+            b0 = fma(yv, yv, b0);
+            c0 = fma(xv, yv, c0);
+          }
         }
-        a = group_sum(a, G, gmask);
-        b = group_sum(b, G, gmask);
-        c = group_sum(c, G, gmask);
-        if (c != T(0) && fabs(c) > tol * dsqrt(a) * dsqrt(b)) {
-          const T zeta = (b - a) / (T(2) * c);
+        T a = a0 + a1, b = b0 + b1, c = c0 + c1;
+        for (int off = G >> 1; off > 0; off >>= 1) {
+          a += __shfl_xor_sync(gmask, a, off);
+          b += __shfl_xor_sync(gmask, b, off);
+          c += __shfl_xor_sync(gmask, c, off);
+        }
+        const T ab = a * b;
+        if (ab > T(0) && c * c > tol2 * ab) {
+          // tan of the rotation angle: the root of t^2 + 2 zeta t - 1 = 0 of
+          // smaller magnitude, zeta = (b - a) / (2c)
+          const T zeta = (b - a) * fast_rcp(T(2) * c);
           const T az = fabs(zeta);
           T t;
           if (az > T(1)) {
-            const T iz = T(1) / az;
-            t = T(1) / (az * (T(1) + dsqrt(T(1) + iz * iz)));
+            const T iz = fast_rcp(az);
+            t = fast_rcp(az * (T(1) + T(1) / rsq(T(1) + iz * iz)));
           } else {
-            t = T(1) / (az + dsqrt(T(1) + az * az));
+            t = fast_rcp(az + T(1) / rsq(T(1) + az * az));
           }
           if (zeta < T(0)) t = -t;
-          const T cs = T(1) / dsqrt(T(1) + t * t);
+          const T cs = rsq(T(1) + t * t);
           const T sn = cs * t;
-          for (int i = lane; i < nr; i += G) {
-            const T xi = x[i], yi = y[i];
-            x[i] = cs * xi - sn * yi;
-            y[i] = sn * xi + cs * yi;
+#pragma unroll
+          for (int u = 0; u < RMAX; ++u) {
+            x[u * G] = cs * xr[u] - sn * yr[u];
+            y[u * G] = sn * xr[u] + cs * yr[u];
           }
           if (WANT_V) {
-            T* vx = Vw + (int64_t)p * n;
-            T* vy = Vw + (int64_t)q * n;
+            T* vx = Vw + (int64_t)p * ldv;
+            T* vy = Vw + (int64_t)q * ldv;
             for (int i = lane; i < nc; i += G) {
-              const T xi = vx[i], yi = vy[i];
-              vx[i] = cs * xi - sn * yi;
-              vy[i] = sn * xi + cs * yi;
+              const T xv = vx[i], yv = vy[i];
+              vx[i] = cs * xv - sn * yv;
+              vy[i] = sn * xv + cs * yv;
             }
           }
           rotated = 1;
@@ -271,13 +378,17 @@ __global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict_
     converged = !__syncthreads_or(rotated);
   }
   if (!converged && tid == 0 && st) atomicAdd(&st->not_converged, 1);
+  if (tid == 0 && st) {
+    atomicAdd(&st->sweeps, sweep);
+    atomicAdd(&st->cores, 1);
+  }
 
   // ---- singular values = column norms, sorted descending
   for (int j = gid; j < nc; j += ngroups) {
     const T* x = Mw + (int64_t)j * ldm;
     T a = T(0);
     for (int i = lane; i < nr; i += G) a += x[i] * x[i];
-    a = group_sum(a, G, gmask);
+    for (int off = G >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(gmask, a, off);
     if (lane == 0) sig_s[j] = isfinite(a) ? dsqrt(a) : T(-1);
   }
   __syncthreads();
@@ -350,7 +461,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const JacobiTask<T>* __restrict_
   if (WANT_V && tk.V) {
     for (int e = tid; e < nc * tk.ucap; e += nt) {
       const int i = e / tk.ucap, c = e % tk.ucap;
-      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * n + i] : T(0);
+      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * ldv + i] : T(0);
     }
   }
 }
@@ -507,32 +618,61 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
   return cudaGetLastError();
 }
 
+// Lanes per pair G and rows per lane RMAX for a launch: all pairs of a round
+// at once when they fit 512 threads, else groups loop over pairs.
+static void jacobi_shape(int nrcap, int nccap, int& G, int& rmax) {
+  const int npairs = (nccap + (nccap & 1)) / 2;
+  G = 32;
+  while (G > 8 && npairs * G > 512) G >>= 1;
+  int need = (nrcap + G - 1) / G;
+  while (need > 32 && G < 32) {
+    G <<= 1;
+    need = (nrcap + G - 1) / G;
+  }
+  rmax = need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : 32;
+}
+
+template <class T, bool V>
+static cudaError_t launch_jacobi_v(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, TruncParams tp,
+                                   DevStatus* st, cudaStream_t s) {
+  int G, rmax;
+  jacobi_shape(nrcap, nccap, G, rmax);
+  const size_t bytes = jacobi_work_bytes(nrcap, nccap, V, sizeof(T));
+  const int use_smem = bytes <= 200 * 1024;
+  const size_t dyn = use_smem ? bytes : 0;
+  auto go = [&](auto kern) -> cudaError_t {
+    if (dyn > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<ntasks, 512, dyn, s>>>(tasks, nrcap, nccap, G, tp, st, use_smem);
+    return cudaGetLastError();
+  };
+  switch (rmax) {
+    case 4: return go(k_jacobi<T, V, 4>);
+    case 8: return go(k_jacobi<T, V, 8>);
+    case 16: return go(k_jacobi<T, V, 16>);
+    default: return go(k_jacobi<T, V, 32>);
+  }
+}
+
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                           TruncParams tp, DevStatus* st, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   if (nccap > 512 || nrcap > 512) return cudaErrorInvalidValue;
-  const size_t bytes = jacobi_work_bytes(nrcap, nccap, want_v, sizeof(T));
-  const int use_smem = bytes <= 200 * 1024;
-  const int threads = (nrcap >= 64 || nccap >= 64) ? 512 : 256;
-  cudaError_t e = cudaSuccess;
-  if (want_v) {
-    if (use_smem && bytes > 48 * 1024)
-      e = cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    k_jacobi<T, true><<<ntasks, threads, use_smem ? bytes : 0, s>>>(tasks, nrcap, nccap, tp, st, use_smem);
-  } else {
-    if (use_smem && bytes > 48 * 1024)
-      e = cudaFuncSetAttribute(k_jacobi<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    k_jacobi<T, false><<<ntasks, threads, use_smem ? bytes : 0, s>>>(tasks, nrcap, nccap, tp, st, use_smem);
-  }
-  return cudaGetLastError();
+  return want_v ? launch_jacobi_v<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s)
+                : launch_jacobi_v<T, false>(tasks, ntasks, nrcap, nccap, tp, st, s);
 }
 
+static void jacobi_shape(int nrcap, int nccap, int& G, int& rmax);
 size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem) {
   const int ncc = nccap + (nccap & 1);
-  return ((size_t)nrcap * ncc + (want_v ? (size_t)ncc * ncc : 0)) * elem;
+  int G, rmax;
+  jacobi_shape(nrcap, nccap, G, rmax);
+  const size_t m = (size_t)jacobi_ld(G * rmax, (int)elem) * ncc;
+  const size_t v = want_v ? (size_t)jacobi_ld(ncc, (int)elem) * ncc : 0;
+  return (m + v) * elem;
 }
 bool jacobi_uses_smem(int nrcap, int nccap, bool want_v, size_t elem) {
   return jacobi_work_bytes(nrcap, nccap, want_v, elem) <= 200 * 1024;

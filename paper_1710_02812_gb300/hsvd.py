@@ -25,7 +25,9 @@ WHERE = {"host": 0, "device": 1}
 
 EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd_factors",
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
-            "hsvd_tree_levels", "hsvd_jacobi_pair")
+            "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
+            "hsvd_set_timing", "hsvd_step_times")
+STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs"}
 
 
 class HsvdError(RuntimeError):
@@ -43,7 +45,8 @@ class Options(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("not_converged", ctypes.c_int32), ("chol_dropped", ctypes.c_int32),
                 ("nonfinite", ctypes.c_int32), ("min_rank", ctypes.c_int32),
-                ("max_rank", ctypes.c_int32)]
+                ("max_rank", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
+                ("jacobi_cores", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,6 +89,15 @@ def lib():
         L.hsvd_tree_levels.restype = i32
         L.hsvd_jacobi_pair.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hsvd_jacobi_pair.restype = ctypes.c_int
+        L.hsvd_step_count.argtypes = [P]
+        L.hsvd_step_count.restype = i32
+        L.hsvd_step_info.argtypes = [P, i32, ctypes.c_char_p, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.hsvd_step_info.restype = ctypes.c_int
+        L.hsvd_set_timing.argtypes = [P, i32]
+        L.hsvd_set_timing.restype = ctypes.c_int
+        L.hsvd_step_times.argtypes = [P, ctypes.POINTER(dbl), i32, ctypes.POINTER(i32)]
+        L.hsvd_step_times.restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -162,6 +174,32 @@ def hsvd_launches_per_run(plan) -> int:
 
 def hsvd_destroy(plan):
     lib().hsvd_destroy(plan)
+
+
+def hsvd_step_count(plan) -> int:
+    return int(lib().hsvd_step_count(plan))
+
+
+def hsvd_step_info(plan, i: int) -> dict:
+    name = ctypes.create_string_buffer(96)
+    kind, tasks, dim = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hsvd_step_info(plan, i, name, 96, ctypes.byref(kind), ctypes.byref(tasks), ctypes.byref(dim),
+                                ctypes.byref(fl), ctypes.byref(by)), "hsvd_step_info")
+    return {"name": name.value.decode(), "kind": STEP_KIND.get(kind.value, "other"), "tasks": tasks.value,
+            "dim": dim.value, "flops": fl.value, "bytes": by.value}
+
+
+def hsvd_set_timing(plan, on: bool):
+    _check(lib().hsvd_set_timing(plan, 1 if on else 0), "hsvd_set_timing")
+
+
+def hsvd_step_times(plan):
+    n = hsvd_step_count(plan)
+    arr = (ctypes.c_double * max(1, n))()
+    runs = ctypes.c_int32()
+    _check(lib().hsvd_step_times(plan, arr, n, ctypes.byref(runs)), "hsvd_step_times")
+    return [arr[i] for i in range(n)], runs.value
 
 
 def hsvd_tree_levels(count: int) -> int:
@@ -270,3 +308,12 @@ class Plan:
     @property
     def launches_per_run(self):
         return hsvd_launches_per_run(self._h)
+
+    def steps(self):
+        return [hsvd_step_info(self._h, i) for i in range(hsvd_step_count(self._h))]
+
+    def set_timing(self, on=True):
+        hsvd_set_timing(self._h, on)
+
+    def step_times(self):
+        return hsvd_step_times(self._h)

@@ -158,7 +158,8 @@ def test_fp32_exact_rank_recovery():
 def test_fp32_batch_of_uneven_matrices():
     sizes = [(600, 450, 9), (1030, 700, 20), (300, 1200, 14), (129, 131, 5)]
     xs = [W.ragged_matrix(m, n, r, tag=i) for i, (m, n, r) in enumerate(sizes)]
-    outs, st, _ = run_gpu(xs, 256, 256, "fixed_k", 24, "f32")
+    # the planted tails sit within 2x of the block noise level: more power steps
+    outs, st, _ = run_gpu(xs, 256, 256, "fixed_k", 24, "f32", power_iters=4)
     for (m, n, r), x, got in zip(sizes, xs, outs):
         ref = oracle_run(x, 256, 256, "fixed_k", 24, "f32")
         # k = 24 exceeds every planted rank: only the planted part is gated
