@@ -199,6 +199,36 @@ hsvd_status hsvd_set_timing(hsvd_plan_t plan, int32_t on);
  * number of timed runs into *runs (either may be NULL). */
 hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* runs);
 
+/* ---- no-allocation variant (no counterpart in the paper) ----
+ * hsvd_block_svd_noalloc -- the rank-k SVD of ONE block, the level-0 step
+ * of the path, for callers that cannot allocate device memory (code running
+ * under an allocator it does not own, memory-capped services, or work that
+ * must not add allocations while other kernels are in flight).  It calls no
+ * cudaMalloc / cudaFree: every intermediate lives in one fixed device array
+ * inside the library (about 3.5 MB, held by every device that loads the
+ * library until the process exits).
+ *   A       device, row-major m x n FP32, leading dimension lda >= n (read only)
+ *   k       rank (1..HSVD_NOALLOC_MAX_K); m, n in 1..HSVD_NOALLOC_MAX_DIM
+ *   power_iters   power steps of the range finder (0..8)
+ *   U       device, m x k column-major FP32, ldu >= m: the first r columns
+ *           are written (r = the rank, numerically zero values dropped)
+ *   S       device, k FP32 singular values, descending, zero past r
+ *   rank    device int32 receiving r
+ * Asynchronous on `stream`.  Sizes beyond the limits return
+ * HSVD_EUNSUPPORTED; bad pointers or shapes HSVD_EINVAL.  The first call on
+ * a device resolves the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call shares the
+ * one array: calls that overlap on the GPU (two streams, two host threads)
+ * race and corrupt each other; serialise them.  The sketch matrix is the one
+ * a plan with the default seed uses, so U and S agree with hsvd_run on a
+ * 1 x 1 grid (block = whole matrix, FIXED_K k, PREC_F32, same power_iters)
+ * within the FP32 tolerance. */
+#define HSVD_NOALLOC_MAX_DIM 1024
+#define HSVD_NOALLOC_MAX_K 64
+hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32_t m, int32_t n, int32_t k,
+                                   int32_t power_iters, float* U, int64_t ldu, float* S, int32_t* rank,
+                                   void* stream);
+
 /* hsvd_destroy -- free everything the plan owns; NULL is accepted. */
 void hsvd_destroy(hsvd_plan_t plan);
 

@@ -26,7 +26,7 @@ WHERE = {"host": 0, "device": 1}
 EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd_factors",
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
-            "hsvd_set_timing", "hsvd_step_times")
+            "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs"}
 
 
@@ -98,6 +98,8 @@ def lib():
         L.hsvd_set_timing.restype = ctypes.c_int
         L.hsvd_step_times.argtypes = [P, ctypes.POINTER(dbl), i32, ctypes.POINTER(i32)]
         L.hsvd_step_times.restype = ctypes.c_int
+        L.hsvd_block_svd_noalloc.argtypes = [P, i64, i32, i32, i32, i32, P, i64, P, P, P]
+        L.hsvd_block_svd_noalloc.restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -212,6 +214,15 @@ def hsvd_jacobi_pair(n: int, rnd: int, slot: int):
     if code != HSVD_OK:
         raise HsvdError(code, "hsvd_jacobi_pair")
     return p.value, q.value
+
+
+def hsvd_block_svd_noalloc(A, m, n, k, power_iters, U, S, rank, stream=None, lda=None, ldu=None):
+    """Rank-k SVD of one block with no device allocation: A (m x n, row
+    major), U (column-major m x k storage, e.g. a k x m row-major tensor),
+    S (k) and rank (one int32) are CUDA tensors; returns the status code."""
+    return lib().hsvd_block_svd_noalloc(A.data_ptr(), lda if lda is not None else A.stride(0), m, n, k,
+                                        power_iters, U.data_ptr(), ldu if ldu is not None else m, S.data_ptr(),
+                                        rank.data_ptr(), _stream_ptr(stream))
 
 
 # ------------------------------------------------------------------ wrapper
