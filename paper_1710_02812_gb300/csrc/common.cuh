@@ -76,6 +76,11 @@ struct GemmItem {
   int task, mt, nt, kc;
 };
 
+// Output tile of the GEMM kernels: FP32 accumulation uses 128 x 64 tiles,
+// FP64 64 x 64.  Items and split-K partial buffers are laid out in tiles.
+constexpr int gemm_tile_m(size_t acc_elem) { return acc_elem == 4 ? 128 : 64; }
+constexpr int GEMM_TILE_N = 64;
+
 // ---------------------------------------------------------------- small tasks
 // Cholesky of a k x k Gram matrix G with relative pivot dropping, returning
 // the upper factor R (G ~= R^T R) and its inverse (dropped directions have
@@ -143,9 +148,11 @@ cudaError_t launch_gemm_tn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* it
 template <class TA, class TB, class TC>
 cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                                cudaStream_t s);
+// with_product: some task has Rprev (the launch stages R2 and R1 in shared
+// memory for the product R2 R1).
 template <class T>
 cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
-                        cudaStream_t s);
+                        cudaStream_t s, bool with_product);
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                           TruncParams tp, DevStatus* st, cudaStream_t s);

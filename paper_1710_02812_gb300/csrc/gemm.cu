@@ -10,6 +10,8 @@
 // One launch serves every task of a tree level: blockIdx.x indexes a work
 // item list (task, tile row, tile column, K chunk) built at plan time.  Task
 // extents may be run-time ranks (Dim::dyn); tiles past them exit early.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hsvd {
@@ -233,13 +235,219 @@ __global__ void __launch_bounds__(NT) k_gemm_reduce(const GemmTask<TA, TB, TC>* 
   }
 }
 
+// ---------------------------------------------------------------- v2 (FP32)
+// 128 x 64 CTA tiles, BK = 16, 256 threads each computing 8 x 4 outputs;
+// the next K tile is loaded into registers while the current one is used
+// (register double buffering); 16-byte vector loads when the tile lies fully
+// inside the operand and its rows are 16-byte aligned, guarded scalar loads
+// otherwise.  Items address 128 x 64 tiles (mt counts 128-row tiles).
+constexpr int BM2 = 128, BN2 = 64, BK2 = 16;
+
+__device__ __forceinline__ void load8(const float* p, float* d) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+  d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float* d) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(h[i]);
+    d[2 * i] = f.x;
+    d[2 * i + 1] = f.y;
+  }
+}
+template <class T>
+__device__ __forceinline__ bool aligned16(const T* p, int64_t ld) {
+  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0);
+}
+
+// IS_TN: C = A^T B with A stored K x M; else C = [A | A2] B with A stored M x K.
+template <class TA, bool IS_TN>
+__global__ void __launch_bounds__(256) k_gemm2(const GemmTask<TA, float, float>* __restrict__ tasks,
+                                               const GemmItem* __restrict__ items, const MatRef* __restrict__ mats) {
+  __shared__ __align__(16) float As[2][BK2][BM2 + 4];
+  __shared__ __align__(16) float Bs[2][BK2][BN2 + 4];
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask<TA, float, float>& tk = tasks[it.task];
+  const int M = eff(tk.M), N = eff(tk.N);
+  const int K1 = eff(tk.K);
+  const int K2 = (!IS_TN && tk.A2) ? eff(tk.K2) : 0;
+  const int Kt = K1 + K2;
+  const int m0 = it.mt * BM2, n0 = it.nt * BN2;
+  if (m0 >= M || n0 >= N) return;
+  int kb = 0, ke = Kt;
+  if (tk.kchunk > 0) {
+    kb = it.kc * tk.kchunk;
+    ke = min(Kt, kb + tk.kchunk);
+  }
+  const TA* A = tk.A;
+  int64_t lda = tk.lda;
+  if (tk.mat >= 0) {
+    const MatRef mr = mats[tk.mat];
+    A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+    lda = mr.ld;
+  }
+  const TA* A2 = tk.A2;
+  const int64_t lda2 = tk.lda2;
+  const float* B = tk.B;
+  const int64_t ldb = tk.ldb;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const bool avec = aligned16(A, lda) && (K2 == 0 || aligned16(A2, lda2));
+  const bool bvec = aligned16(B, ldb);
+
+  // loader coordinates
+  // NN A tile: 128 rows x 16 k: thread -> row (tid >> 1), k (tid & 1) * 8
+  // TN A tile: 16 k x 128 m:   thread -> k (tid >> 4), m (tid & 15) * 8
+  // B tile:    16 k x 64 n:    thread -> k (tid >> 4), n (tid & 15) * 4
+  float ra[8], rb[4];
+  auto load_tiles = [&](int k0) {
+    if (!IS_TN) {
+      const int r = tid >> 1, kk = (tid & 1) * 8;
+      const int gm = m0 + r, gk = k0 + kk;
+      // vector path: 8 elements inside one segment, 16-byte aligned in it
+      constexpr int VE = 16 / (int)sizeof(TA);
+      if (avec && gm < M && gk + 8 <= ke && (gk + 8 <= K1 || (gk >= K1 && ((gk - K1) % VE) == 0))) {
+        if (gk < K1)
+          load8(A + (int64_t)gm * lda + gk, ra);
+        else
+          load8(A2 + (int64_t)gm * lda2 + (gk - K1), ra);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int g = gk + i;
+          float v = 0.f;
+          if (gm < M && g < ke) v = (g < K1) ? cvt<float>(A[(int64_t)gm * lda + g]) : cvt<float>(A2[(int64_t)gm * lda2 + (g - K1)]);
+          ra[i] = v;
+        }
+      }
+    } else {
+      const int kk = tid >> 4, mm = (tid & 15) * 8;
+      const int gk = k0 + kk, gm = m0 + mm;
+      if (avec && gk < ke && gm + 8 <= M) {
+        load8(A + (int64_t)gk * lda + gm, ra);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ra[i] = (gk < ke && gm + i < M) ? cvt<float>(A[(int64_t)gk * lda + gm + i]) : 0.f;
+      }
+    }
+    {
+      const int kk = tid >> 4, nn = (tid & 15) * 4;
+      const int gk = k0 + kk, gn = n0 + nn;
+      if (bvec && gk < ke && gn + 4 <= N) {
+        const float4 v = *reinterpret_cast<const float4*>(B + (int64_t)gk * ldb + gn);
+        rb[0] = v.x; rb[1] = v.y; rb[2] = v.z; rb[3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rb[i] = (gk < ke && gn + i < N) ? B[(int64_t)gk * ldb + gn + i] : 0.f;
+      }
+    }
+  };
+  auto store_tiles = [&](int buf) {
+    if (!IS_TN) {
+      const int r = tid >> 1, kk = (tid & 1) * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[buf][kk + i][r] = ra[i];
+    } else {
+      const int kk = tid >> 4, mm = (tid & 15) * 8;
+      *reinterpret_cast<float4*>(&As[buf][kk][mm]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+      *reinterpret_cast<float4*>(&As[buf][kk][mm + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+    }
+    const int kk = tid >> 4, nn = (tid & 15) * 4;
+    *reinterpret_cast<float4*>(&Bs[buf][kk][nn]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+  };
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (kb < ke) {
+    load_tiles(kb);
+    store_tiles(0);
+  }
+  __syncthreads();
+  for (int k0 = kb; k0 < ke; k0 += BK2) {
+    const bool more = k0 + BK2 < ke;
+    if (more) load_tiles(k0 + BK2);
+#pragma unroll
+    for (int kk = 0; kk < BK2; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) store_tiles(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+
+  if (tk.partial) {
+    float* P = tk.partial + ((int64_t)(it.kc * tk.mtiles + it.mt) * tk.ntiles + it.nt) * (BM2 * BN2);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<float4*>(&P[(ty * 8 + i) * BN2 + tx * 4]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    return;
+  }
+  const float alpha = tk.alpha, beta = tk.beta;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + ty * 8 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      float v = alpha * acc[i][j];
+      if (tk.C0) v += beta * tk.C0[(int64_t)gm * tk.ldc0 + gn];
+      tk.C[(int64_t)gm * tk.ldc + gn] = v;
+    }
+  }
+}
+
+// Sum the K-chunk partial tiles (128 x 64) of one (task, tile) in chunk order.
+template <class TA>
+__global__ void __launch_bounds__(256) k_gemm2_reduce(const GemmTask<TA, float, float>* __restrict__ tasks,
+                                                      const GemmItem* __restrict__ items) {
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask<TA, float, float>& tk = tasks[it.task];
+  const int M = eff(tk.M), N = eff(tk.N);
+  const int m0 = it.mt * BM2, n0 = it.nt * BN2;
+  if (m0 >= M || n0 >= N) return;
+  const int64_t tile_stride = (int64_t)tk.mtiles * tk.ntiles * (BM2 * BN2);
+  const float* P = tk.partial + ((int64_t)it.mt * tk.ntiles + it.nt) * (BM2 * BN2);
+  for (int e = threadIdx.x; e < BM2 * BN2; e += 256) {
+    const int r = e / BN2, c = e % BN2;
+    const int gm = m0 + r, gn = n0 + c;
+    if (gm >= M || gn >= N) continue;
+    float sacc = 0.f;
+    for (int kc = 0; kc < tk.nkc; ++kc) sacc += P[kc * tile_stride + e];
+    float v = tk.alpha * sacc;
+    if (tk.C0) v += tk.beta * tk.C0[(int64_t)gm * tk.ldc0 + gn];
+    tk.C[(int64_t)gm * tk.ldc + gn] = v;
+  }
+}
+
 }  // namespace
 
 template <class TA, class TB, class TC>
 cudaError_t launch_gemm_nn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                            const MatRef* mats, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  k_gemm_nn<TA, TB, TC, 32><<<nitems, NT, 0, s>>>(tasks, items, mats);
+  if constexpr (std::is_same<TC, float>::value && std::is_same<TB, float>::value)
+    k_gemm2<TA, false><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else
+    k_gemm_nn<TA, TB, TC, 32><<<nitems, NT, 0, s>>>(tasks, items, mats);
   return cudaGetLastError();
 }
 
@@ -247,7 +455,10 @@ template <class TA, class TB, class TC>
 cudaError_t launch_gemm_tn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                            const MatRef* mats, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  k_gemm_tn<TA, TB, TC, 16><<<nitems, NT, 0, s>>>(tasks, items, mats);
+  if constexpr (std::is_same<TC, float>::value && std::is_same<TB, float>::value)
+    k_gemm2<TA, true><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else
+    k_gemm_tn<TA, TB, TC, 16><<<nitems, NT, 0, s>>>(tasks, items, mats);
   return cudaGetLastError();
 }
 
@@ -255,7 +466,10 @@ template <class TA, class TB, class TC>
 cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                                cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  k_gemm_reduce<TA, TB, TC><<<nitems, NT, 0, s>>>(tasks, items);
+  if constexpr (std::is_same<TC, float>::value && std::is_same<TB, float>::value)
+    k_gemm2_reduce<TA><<<nitems, 256, 0, s>>>(tasks, items);
+  else
+    k_gemm_reduce<TA, TB, TC><<<nitems, NT, 0, s>>>(tasks, items);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,6 @@ namespace {
 constexpr int NA_MAX_DIM = HSVD_NOALLOC_MAX_DIM;  // m, n <= 1024
 constexpr int NA_MAX_K = HSVD_NOALLOC_MAX_K;      // k <= 64
 constexpr int NA_MAX_KP = 2 * NA_MAX_K;          // sketch width <= 128
-constexpr int NA_TILE = 64;
 constexpr size_t NA_TABLE_BYTES = 256 * 1024;
 
 // Float layout of the scratch array (offsets in floats, 64-float aligned).
@@ -98,8 +97,8 @@ GT gt_blank() {
 // Tile items of a GEMM without K splitting (every K here is <= 1024).
 std::vector<GemmItem> items_of(const GT& g) {
   std::vector<GemmItem> it;
-  for (int mt = 0; mt < cdiv(g.M.cap, NA_TILE); ++mt)
-    for (int nt = 0; nt < cdiv(g.N.cap, NA_TILE); ++nt) it.push_back(GemmItem{0, mt, nt, 0});
+  for (int mt = 0; mt < cdiv(g.M.cap, gemm_tile_m(sizeof(float))); ++mt)
+    for (int nt = 0; nt < cdiv(g.N.cap, GEMM_TILE_N); ++nt) it.push_back(GemmItem{0, mt, nt, 0});
   return it;
 }
 
@@ -175,8 +174,8 @@ extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32
     g.K2 = Dim{0, nullptr};
     g.N = N;
     g.mat = mat;
-    g.mtiles = cdiv(M, NA_TILE);
-    g.ntiles = cdiv(N.cap, NA_TILE);
+    g.mtiles = cdiv(M, gemm_tile_m(sizeof(float)));
+    g.ntiles = cdiv(N.cap, GEMM_TILE_N);
     g.nkc = 1;
     gemm(g, false);
   };
@@ -194,12 +193,14 @@ extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32
     g.K2 = Dim{0, nullptr};
     g.N = Dim{N, nullptr};
     g.mat = mat;
-    g.mtiles = cdiv(M, NA_TILE);
-    g.ntiles = cdiv(N, NA_TILE);
+    g.mtiles = cdiv(M, gemm_tile_m(sizeof(float)));
+    g.ntiles = cdiv(N, GEMM_TILE_N);
     g.nkc = 1;
     gemm(g, true);
   };
+  std::vector<char> chol_prod;  // per chol launch: has an R2 R1 product
   auto chol = [&](float* Rout, const float* Rprev) {
+    chol_prod.push_back(Rprev != nullptr);
     CholTask<float> c;
     std::memset(&c, 0, sizeof(c));
     c.G = G;
@@ -214,7 +215,7 @@ extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32
     L l;
     l.kind = 4;
     l.t = tb.put(&c, sizeof(c));
-    l.i = 0;
+    l.i = chol_prod.size() - 1;
     l.n = 1;
     l.kcap = kp;
     launches.push_back(l);
@@ -301,7 +302,7 @@ extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32
       case 2: e = launch_gemm_tn<float, float, float>(static_cast<const GT*>(t), it, l.n, mats, s); break;
       case 4:
         e = launch_chol<float>(static_cast<const CholTask<float>*>(t), 1, l.kcap, dst, 50.0 * 5.9604644775390625e-08,
-                               s);
+                               s, chol_prod[l.i] != 0);
         break;
       default:
         e = launch_jacobi<float>(static_cast<const JacobiTask<float>*>(t), 1, l.kcap, l.kcap, false, tp, dst, s);

@@ -26,7 +26,6 @@ namespace hsvd {
 
 namespace {
 
-constexpr int TILE = 64;
 constexpr int KCHUNK = 1024;
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -244,19 +243,22 @@ struct Builder {
 
   template <class G>
   void finish_items(std::vector<G>& tasks, bool is_tn, std::vector<GemmItem>& items, std::vector<GemmItem>& red) {
+    constexpr int TM = gemm_tile_m(sizeof(T)), TN = GEMM_TILE_N;
     for (size_t t = 0; t < tasks.size(); ++t) {
       G& g = tasks[t];
-      g.mtiles = cdiv(g.M.cap, TILE);
-      g.ntiles = cdiv(g.N.cap, TILE);
+      g.mtiles = cdiv(g.M.cap, TM);
+      g.ntiles = cdiv(g.N.cap, TN);
       g.nkc = 1;
       g.kchunk = 0;
       g.partial = nullptr;
       if (g.M.cap <= 0 || g.N.cap <= 0) continue;
       const int ktot = g.K.cap + (is_tn ? 0 : g.K2.cap);
-      if (ktot > KCHUNK) {
-        g.kchunk = KCHUNK;
-        g.nkc = cdiv(ktot, KCHUNK);
-        g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * TILE * TILE);
+      // long K with few output tiles: split finer so the launch fills the GPU
+      const int chunk = (ktot > KCHUNK && g.mtiles * g.ntiles <= 2) ? KCHUNK / 4 : KCHUNK;
+      if (ktot > chunk) {
+        g.kchunk = chunk;
+        g.nkc = cdiv(ktot, chunk);
+        g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * TM * TN);
         for (int mt = 0; mt < g.mtiles; ++mt)
           for (int nt = 0; nt < g.ntiles; ++nt) red.push_back(GemmItem{(int)t, mt, nt, 0});
       }
@@ -391,14 +393,16 @@ struct Builder {
   // -------------------------------------------------------------- small steps
   void emit_chol(const std::string& name, std::vector<CholTask<T>> tasks, int kcapl) {
     if (tasks.empty()) return;
+    bool prod = false;
+    for (const auto& t : tasks) prod = prod || t.Rprev != nullptr;
     if (!chol_uses_smem(kcapl, sizeof(T)))
       for (auto& t : tasks) t.work = alloc<T>((size_t)kcapl * kcapl);
     PlanImpl* p = &P;
     const size_t bt = P.add_blob(tasks);
     const int nt = (int)tasks.size();
     const double tau = P.tau;
-    P.steps.push_back(Step{name, [p, bt, nt, kcapl, tau](cudaStream_t s) {
-                             return launch_chol<T>(p->table<CholTask<T>>(bt), nt, kcapl, p->d_status, tau, s);
+    P.steps.push_back(Step{name, [p, bt, nt, kcapl, tau, prod](cudaStream_t s) {
+                             return launch_chol<T>(p->table<CholTask<T>>(bt), nt, kcapl, p->d_status, tau, s, prod);
                            }});
     {
       double fl = 0, by = 0;

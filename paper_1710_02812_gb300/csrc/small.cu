@@ -44,9 +44,9 @@ __device__ __forceinline__ T dsqrt(T x) {
 // the unit lower inverse L^{-1}.  R = D^{-1/2} U S^{-1}, R^{-1} = S L^{-T} D^{-1/2}.
 // Thread (ty, tx) of the 16 x 16 CTA owns the entries (i, c) with
 // i = ty mod 16, c = tx mod 16, so no index division is needed.
-template <class T>
+template <class T, bool SMEM>
 __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ tasks, int kcap,
-                                              DevStatus* __restrict__ st, T tau, int use_smem) {
+                                              DevStatus* __restrict__ st, T tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T sc[256];
   __shared__ T dpv[256];
@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ ta
   const CholTask<T>& tk = tasks[blockIdx.x];
   const int k = eff(tk.k);
   if (k <= 0) return;
-  T* M = use_smem ? reinterpret_cast<T*>(smem_raw) : tk.work;
+  // SMEM: the working copy is addressed as shared memory (32-bit offsets);
+  // otherwise it lives in the task's global scratch.
+  T* __restrict__ M = SMEM ? reinterpret_cast<T*>(smem_raw) : tk.work;
   const int ld = k;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ty = tid >> 4, tx = tid & 15;
@@ -134,6 +136,319 @@ __global__ void __launch_bounds__(256) k_chol(const CholTask<T>* __restrict__ ta
   }
 }
 
+// Register-tiled shared-memory variant for k <= 16 KB: thread (ty, tx)
+// owns rows i = ty + 16a and columns c = tx + 16b (a, b < KB).  Each step j
+// caches row j's entries of its columns and its rows' multipliers in
+// registers, then updates its tile, so loads and stores of the step are
+// independent.  The product R2 R1 (CholeskyQR2) reads R1 staged in shared
+// memory.
+template <class T, int KB>
+__global__ void __launch_bounds__(256) k_chol_tiled(const CholTask<T>* __restrict__ tasks,
+                                                    DevStatus* __restrict__ st, T tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* __restrict__ M = reinterpret_cast<T*>(smem_raw);
+  __shared__ T sc[16 * KB];
+  __shared__ T dpv[16 * KB];
+  __shared__ int bad;
+  const CholTask<T>& tk = tasks[blockIdx.x];
+  const int k = eff(tk.k);
+  if (k <= 0) return;
+  const int ld = 16 * KB + 1;  // odd row stride: columns tx + 16b fall in distinct banks
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = tid; j < k; j += 256) {
+    const T g = tk.G[(int64_t)j * tk.ldg + j];
+    if (!isfinite(g)) bad = 1;
+    sc[j] = (g > T(0) && isfinite(g)) ? T(1) / dsqrt(g) : T(0);
+  }
+  __syncthreads();
+  if (tid == 0 && bad && st) atomicAdd(&st->nonfinite, 1);
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      T v = T(0);
+      if (i < k && c < k && c >= i) v = tk.G[(int64_t)i * tk.ldg + c] * sc[i] * sc[c];
+      M[i * ld + c] = v;
+    }
+  }
+  __syncthreads();
+
+  int ndrop = 0;
+  for (int j = 0; j < k; ++j) {
+    const T d = M[j * ld + j];
+    const bool drop = !(sc[j] > T(0)) || !(d > tau);
+    T rj[KB], f[KB];
+#pragma unroll
+    for (int b = 0; b < KB; ++b) rj[b] = M[j * ld + tx + 16 * b];
+    const T dinv = drop ? T(0) : T(1) / d;
+#pragma unroll
+    for (int a = 0; a < KB; ++a) f[a] = M[j * ld + ty + 16 * a] * dinv;
+    __syncthreads();  // row j read by everyone before rows > j change
+    if (drop) {
+      if (tid == 0) dpv[j] = T(0);
+      ++ndrop;
+      continue;
+    }
+    if (tid == 0) dpv[j] = d;
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const int i = ty + 16 * a;
+      if (i <= j || i >= k) continue;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int c = tx + 16 * b;
+        if (c >= k) continue;
+        if (c >= i || c < j)
+          M[i * ld + c] -= f[a] * rj[b];
+        else if (c == j)
+          M[i * ld + j] = -f[a];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && ndrop > 0 && st) atomicAdd(&st->chol_dropped, ndrop);
+
+  if (tk.Rinv) {
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const int l = ty + 16 * a;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int j = tx + 16 * b;
+        if (l >= k || j >= k) continue;
+        T v = T(0);
+        if (l <= j && dpv[j] > T(0)) v = sc[l] * ((l == j) ? T(1) : M[j * ld + l]) / dsqrt(dpv[j]);
+        tk.Rinv[(int64_t)l * tk.ldri + j] = v;
+      }
+    }
+  }
+  __syncthreads();
+  // R[j][c] = M[j][c] / sqrt(d_j) / s_c for c >= j; the strictly lower part
+  // receives R1^T (R1 = Rprev) for the product below.
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int j = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      if (j >= k || c >= k) continue;
+      T v = T(0);
+      if (c >= j) {
+        if (dpv[j] > T(0) && sc[c] > T(0)) v = M[j * ld + c] / dsqrt(dpv[j]) / sc[c];
+      } else if (tk.Rprev) {
+        v = tk.Rprev[(int64_t)c * tk.ldrp + j];  // R1[c][j], c < j
+      }
+      M[j * ld + c] = v;
+    }
+  }
+  __syncthreads();
+  if (!tk.R) return;
+  // R[i][j] = sum_{l=i..j} R2[i][l] R1[l][j]; R1[l][j] = M[j][l] for l < j and
+  // R1[j][j] read from global (the diagonal holds R2).
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int j = tx + 16 * b;
+      if (i >= k || j >= k) continue;
+      T v = T(0);
+      if (j >= i) {
+        if (tk.Rprev) {
+          for (int l = i; l < j; ++l) v += M[i * ld + l] * M[j * ld + l];
+          v += M[i * ld + j] * tk.Rprev[(int64_t)j * tk.ldrp + j];
+        } else {
+          v = M[i * ld + j];
+        }
+      }
+      tk.R[(int64_t)i * tk.ldr + j] = v;
+    }
+  }
+}
+
+// Register-resident variant for k <= 16 KB (KB <= 8): thread (ty, tx) keeps
+// the entries (ty + 16a, tx + 16b) of the working matrix in registers.  Step j
+// broadcasts row j through a double-buffered shared row (one barrier per
+// step); every thread then updates its tile with the cached multipliers.
+// The product R2 R1 of CholeskyQR2 is a register-tiled product over l with
+// R2 and R1 staged in shared memory.
+template <class T, int KB>
+__global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict__ tasks,
+                                                  DevStatus* __restrict__ st, T tau) {
+  constexpr int KM = 16 * KB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* __restrict__ Rs = reinterpret_cast<T*>(smem_raw);  // KM x (KM + 1): R2, then R1 in the second half
+  __shared__ T row[2][KM];
+  __shared__ T sc[KM];
+  __shared__ T dpv[KM];
+  __shared__ int bad;
+  const CholTask<T>& tk = tasks[blockIdx.x];
+  const int k = eff(tk.k);
+  if (k <= 0) return;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = tid; j < k; j += 256) {
+    const T g = tk.G[(int64_t)j * tk.ldg + j];
+    if (!isfinite(g)) bad = 1;
+    sc[j] = (g > T(0) && isfinite(g)) ? T(1) / dsqrt(g) : T(0);
+  }
+  __syncthreads();
+  if (tid == 0 && bad && st) atomicAdd(&st->nonfinite, 1);
+  T m[KB][KB];
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      m[a][b] = (i < k && c < k && c >= i) ? tk.G[(int64_t)i * tk.ldg + c] * sc[i] * sc[c] : T(0);
+    }
+  }
+
+  int ndrop = 0;
+  for (int j = 0; j < k; ++j) {
+    const int buf = j & 1;
+    const int aj = j >> 4;
+    if (ty == (j & 15)) {
+#pragma unroll
+      for (int a = 0; a < KB; ++a)
+        if (a == aj) {
+#pragma unroll
+          for (int b = 0; b < KB; ++b) row[buf][tx + 16 * b] = m[a][b];
+        }
+    }
+    __syncthreads();
+    const T d = row[buf][j];
+    const bool drop = !(sc[j] > T(0)) || !(d > tau);
+    if (tid == 0) dpv[j] = drop ? T(0) : d;
+    if (drop) {  // eliminates nothing; column j below stays zero
+      ++ndrop;
+      continue;
+    }
+    // Rows i > j: upper entries (c >= i) and inverse entries (c < j) get
+    // m[i][c] -= f_i m[j][c]; entry (i, j) becomes -f_i; the entries
+    // j < c < i (below the trailing diagonal) are left alone.
+    const T dinv = T(1) / d;
+    T f[KB], rj[KB];
+#pragma unroll
+    for (int a = 0; a < KB; ++a) f[a] = row[buf][ty + 16 * a] * dinv;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) rj[b] = row[buf][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const int i = ty + 16 * a;
+      if (i <= j) continue;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int c = tx + 16 * b;
+        if (c >= i || c < j)
+          m[a][b] -= f[a] * rj[b];
+        else if (c == j)
+          m[a][b] = -f[a];
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && ndrop > 0 && st) atomicAdd(&st->chol_dropped, ndrop);
+
+  // R^{-1}: entry (i, c), c < i, of the tile is Linv[i][c] -> R^{-1}[c][i]
+  // = s_c Linv[i][c] / sqrt(d_i); the diagonal is s_i / sqrt(d_i).
+  if (tk.Rinv) {
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const int i = ty + 16 * a;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int c = tx + 16 * b;
+        if (i >= k || c >= k || c > i) continue;
+        const T di = dpv[i];
+        const T rs = di > T(0) ? T(1) / dsqrt(di) : T(0);
+        if (c == i) {
+          tk.Rinv[(int64_t)i * tk.ldri + i] = sc[i] * rs;
+        } else {
+          tk.Rinv[(int64_t)c * tk.ldri + i] = sc[c] * m[a][b] * rs;
+          tk.Rinv[(int64_t)i * tk.ldri + c] = T(0);
+        }
+      }
+    }
+  }
+  if (!tk.R) return;
+  // R[i][c] = M[i][c] / sqrt(d_i) / s_c (c >= i)
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+    const T di = (i < k) ? dpv[i] : T(0);
+    const T rs = di > T(0) ? T(1) / dsqrt(di) : T(0);
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      m[a][b] = (i < k && c < k && c >= i && sc[c] > T(0)) ? m[a][b] * rs / sc[c] : T(0);
+    }
+  }
+  if (!tk.Rprev) {
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const int i = ty + 16 * a;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int c = tx + 16 * b;
+        if (i < k && c < k) tk.R[(int64_t)i * tk.ldr + c] = m[a][b];
+      }
+    }
+    return;
+  }
+  // stage R2 (this factor) and R1 (Rprev) in shared memory, then
+  // R[i][c] = sum_l R2[i][l] R1[l][c] with an 8 x 8 register tile per thread.
+  const int lds = KM + 1;
+  T* R2s = Rs;
+  T* R1s = Rs + KM * lds;
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      R2s[i * lds + c] = m[a][b];
+      R1s[i * lds + c] = (i < k && c < k && c >= i) ? tk.Rprev[(int64_t)i * tk.ldrp + c] : T(0);
+    }
+  }
+  __syncthreads();
+  T acc[KB][KB];
+#pragma unroll
+  for (int a = 0; a < KB; ++a)
+#pragma unroll
+    for (int b = 0; b < KB; ++b) acc[a][b] = T(0);
+  for (int l = 0; l < k; ++l) {
+    T ra[KB], rb[KB];
+#pragma unroll
+    for (int a = 0; a < KB; ++a) ra[a] = R2s[(ty + 16 * a) * lds + l];
+#pragma unroll
+    for (int b = 0; b < KB; ++b) rb[b] = R1s[l * lds + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < KB; ++a)
+#pragma unroll
+      for (int b = 0; b < KB; ++b) acc[a][b] = fma(ra[a], rb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < KB; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      if (i < k && c < k) tk.R[(int64_t)i * tk.ldr + c] = acc[a][b];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ Jacobi
 // Round-robin (circle) ordering for n even: slot 0 pairs (r, n-1); slot s>0
 // pairs (r+s, r-s) mod (n-1).  Each unordered pair appears once per sweep and
@@ -167,6 +482,16 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 __host__ __device__ __forceinline__ int jacobi_ld(int nr, int elem) {
   const int period = elem == 8 ? 16 : 32;
   return ((nr + period - 1) / period) * period + period / 4;
+}
+// The same for G lanes per pair (32 / G groups per warp, consecutive groups
+// handle consecutive columns): consecutive columns start G banks apart, so
+// the groups of one warp read disjoint bank ranges (8-byte elements take two
+// banks each; a warp's request spans two wavefronts anyway).
+__host__ __device__ __forceinline__ int jacobi_ld_g(int nr, int elem, int G) {
+  const int period = elem == 8 ? 16 : 32;
+  int ld = ((nr + period - 1) / period) * period;
+  if (G < 32) ld += (elem == 8 && G > 8) ? 8 : G;
+  return ld;
 }
 
 // Householder QR of the n x n column-major matrix A (ld lda) in shared or
@@ -225,8 +550,280 @@ __device__ void householder_r_transpose(T* A, int lda, int n, T* scratch) {
   __syncthreads();
 }
 
-// All n/2 column pairs of a round are processed at once, G lanes per pair,
-// each lane holding at most RMAX rows of the pair in registers.
+// Sort the singular values (column norms in sig_s), choose the rank by the
+// truncation rule and write sigma, the normalised left vectors and, if
+// wanted, the sorted right rotations.
+template <class T, bool WANT_V>
+__device__ void jacobi_finish(const JacobiTask<T>& tk, const T* Mw, int ldm, const T* Vw, int ldv, int nr, int nc,
+                              int k1, int k2, const TruncParams& tp, DevStatus* st, T* sig_s, int* perm,
+                              int* rank_sp) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = tid; j < nc; j += nt) {
+    const T sj = sig_s[j];
+    int pos = 0;
+    for (int i = 0; i < nc; ++i) {
+      const T si = sig_s[i];
+      pos += (si > sj) || (si == sj && i < j);
+    }
+    perm[pos] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int bad = 0;
+    for (int i = 0; i < nc; ++i) bad += sig_s[i] < T(0);
+    if (bad && st) atomicAdd(&st->nonfinite, 1);
+    int r = 0;
+    const double s1 = nc > 0 ? (double)sig_s[perm[0]] : 0.0;
+    if (nc > 0 && s1 > 0.0 && !bad) {
+      int numerical = 0;
+      for (int i = 0; i < nc; ++i) numerical += (double)sig_s[perm[i]] > tp.rank_tol * s1;
+      if (tp.mode == 0) {
+        r = (int)tp.param;
+      } else if (tp.mode == 1) {
+        r = 0;
+        for (int i = 0; i < nc; ++i) r += (double)sig_s[perm[i]] >= tp.param * s1;
+      } else {
+        double total = 0.0;
+        if (tk.energy) {
+          total = (double)*tk.energy;
+        } else if (tk.load == 1) {
+          for (int i = 0; i < k1; ++i) total += (double)tk.s1[i] * (double)tk.s1[i];
+          for (int i = 0; i < k2; ++i) total += (double)tk.s2[i] * (double)tk.s2[i];
+        } else {
+          for (int i = 0; i < nc; ++i) total += (double)sig_s[i] * (double)sig_s[i];
+        }
+        double cum = 0.0;
+        r = nc;
+        for (int i = 0; i < nc; ++i) {
+          const double s = (double)sig_s[perm[i]];
+          cum += s * s;
+          if (cum >= tp.param * total) {
+            r = i + 1;
+            break;
+          }
+        }
+      }
+      r = min(r, numerical);
+      r = min(r, tp.rank_cap);
+      r = min(r, nc);
+      r = min(r, tk.ucap);
+      if (r < 0) r = 0;
+    }
+    *rank_sp = r;
+    if (tk.rank) *tk.rank = r;
+  }
+  __syncthreads();
+  const int r = *rank_sp;
+  if (tk.sig)
+    for (int c = tid; c < tk.ucap; c += nt) tk.sig[c] = (c < r) ? sig_s[perm[c]] : T(0);
+  if (tk.U) {
+    for (int e = tid; e < nr * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      T v = T(0);
+      if (c < r) v = Mw[(int64_t)perm[c] * ldm + i] / sig_s[perm[c]];
+      tk.U[(int64_t)i * tk.ldu + c] = v;
+    }
+  }
+  if (WANT_V && tk.V) {
+    for (int e = tid; e < nc * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * ldv + i] : T(0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+// splitmix64 (Steele, Lea & Flood, 2014) as a counter-based generator, and a
+// Box-Muller transform of two of its outputs per element.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_fill_gaussian(T* out, int64_t count, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)e));
+    const uint64_t b = splitmix64(seed ^ (2 * (uint64_t)e + 1));
+    const double u1 = ((double)(a >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
+    const double u2 = (double)(b >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    out[e] = (T)z;
+  }
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    dst[i * ldd + j] = __float2bfloat16_rn(src[i * lds + j]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ float to_f(T x) {
+  return (float)x;
+}
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+// ||X_blk||_F^2 with per-thread compensated (Kahan) FP32 sums and a
+// fixed-order FP64 combination of the per-thread partials.
+template <class TA, class TO>
+__global__ void __launch_bounds__(256) k_block_energy(const EnergyTask* __restrict__ tasks,
+                                                      const MatRef* __restrict__ mats) {
+  __shared__ double part[256];
+  const EnergyTask tk = tasks[blockIdx.x];
+  const MatRef mr = mats[tk.mat];
+  const TA* A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+  float s = 0.f, comp = 0.f;
+  const int64_t total = (int64_t)tk.h * tk.w;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t i = e / tk.w, j = e % tk.w;
+    const float v = to_f(A[i * mr.ld + j]);
+    const float y = v * v - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  part[threadIdx.x] = (double)s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) acc += part[i];
+    *static_cast<TO*>(tk.out) = (TO)acc;
+  }
+}
+
+// One CTA per column c < rank: find the first row of largest |U[i][c]|, flip
+// the column of U and of V if that entry is negative.
+template <class T>
+__global__ void __launch_bounds__(256) k_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n,
+                                                        const int* rank) {
+  __shared__ T bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.x;
+  if (c >= *rank) return;
+  T best = T(-1);
+  int besti = 0x7fffffff;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T a = fabs(U[(int64_t)i * ldu + c]);
+    if (a > best || (a == best && i < besti)) {
+      best = a;
+      besti = i;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = besti;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      const T ob = bv[threadIdx.x + off];
+      const int oi = bi[threadIdx.x + off];
+      if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = ob;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int imax = bi[0];
+  if (imax >= m) return;
+  const bool neg = U[(int64_t)imax * ldu + c] < T(0);
+  __syncthreads();
+  if (!neg) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) U[(int64_t)i * ldu + c] = -U[(int64_t)i * ldu + c];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * ldv + c] = -V[(int64_t)i * ldv + c];
+}
+
+template <class T>
+__global__ void k_rm_to_cm(const T* __restrict__ src, int64_t lds, int rows, const int* rank, int kcap,
+                           T* __restrict__ dst, int64_t ldd) {
+  const int r = min(*rank, kcap);
+  const int64_t total = (int64_t)rows * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, i = e % rows;
+    dst[c * ldd + i] = src[i * lds + c];
+  }
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int jacobi_pair_host(int n, int r, int s, int* p, int* q) {
+  if (n < 2 || (n & 1) || r < 0 || r >= n - 1 || s < 0 || s >= n / 2) return 1;
+  rr_pair(n, r, s, *p, *q);
+  return 0;
+}
+
+template <class T>
+cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
+                        cudaStream_t s, bool with_product) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (kcap > 256) return cudaErrorInvalidValue;
+  {
+    const int kb = kcap <= 32 ? 2 : kcap <= 64 ? 4 : kcap <= 128 ? 8 : 16;
+    if (kb <= 8) {
+      // shared memory only for staging R2 and R1 of the CholeskyQR2 product
+      const size_t rb = with_product ? 2 * (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T) : 0;
+      auto go = [&](auto kern) -> cudaError_t {
+        if (rb > 48 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);
+          if (e != cudaSuccess) return e;
+        }
+        kern<<<ntasks, 256, rb, s>>>(tasks, st, (T)tau);
+        return cudaGetLastError();
+      };
+      if (kb == 2) return go(k_chol_reg<T, 2>);
+      if (kb == 4) return go(k_chol_reg<T, 4>);
+      return go(k_chol_reg<T, 8>);
+    }
+    const size_t tb = (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T);
+    if (tb <= 200 * 1024) {
+      auto go = [&](auto kern) -> cudaError_t {
+        if (tb > 48 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
+          if (e != cudaSuccess) return e;
+        }
+        kern<<<ntasks, 256, tb, s>>>(tasks, st, (T)tau);
+        return cudaGetLastError();
+      };
+      if (kb == 2) return go(k_chol_tiled<T, 2>);
+      if (kb == 4) return go(k_chol_tiled<T, 4>);
+      if (kb == 8) return go(k_chol_tiled<T, 8>);
+      return go(k_chol_tiled<T, 16>);
+    }
+  }
+  const size_t bytes = (size_t)kcap * kcap * sizeof(T);
+  if (bytes <= 200 * 1024) {
+    if (bytes > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_chol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+    }
+    k_chol<T, true><<<ntasks, 256, bytes, s>>>(tasks, kcap, st, (T)tau);
+  } else {
+    k_chol<T, false><<<ntasks, 256, 0, s>>>(tasks, kcap, st, (T)tau);
+  }
+  return cudaGetLastError();
+}
+
+// Generic core SVD (working copy in shared or global memory): all n/2 column
+// pairs of a round are processed at once, G lanes per pair, each lane holding
+// at most RMAX rows of the pair in registers.
 template <class T, int RMAX>
 struct JacobiOcc {
   // two CTAs per SM when the row registers fit in 64 per thread
@@ -392,230 +989,169 @@ __global__ void __launch_bounds__(512, JacobiOcc<T, RMAX>::value) k_jacobi(const
     if (lane == 0) sig_s[j] = isfinite(a) ? dsqrt(a) : T(-1);
   }
   __syncthreads();
-  for (int j = tid; j < nc; j += nt) {
-    const T sj = sig_s[j];
-    int pos = 0;
-    for (int i = 0; i < nc; ++i) {
-      const T si = sig_s[i];
-      pos += (si > sj) || (si == sj && i < j);
+  jacobi_finish<T, WANT_V>(tk, Mw, ldm, Vw, ldv, nr, nc, k1, k2, tp, st, sig_s, perm, &rank_s);
+}
+
+// Shared-memory specialisation of the core SVD for cores whose working copy
+// fits on chip: G (lanes per pair) and RMAX (rows per lane) are compile-time,
+// the working copy is addressed with 32-bit shared-memory offsets, and the
+// loop stops after a sweep whose largest rotation was below sqrt(tol): the
+// cyclic method converges quadratically, so the off-diagonal left behind is
+// below tol and the verification sweep is skipped.
+template <class T, bool WANT_V, int G, int RMAX>
+__global__ void __launch_bounds__(1024, 1) k_jacobi_sm(const JacobiTask<T>* __restrict__ tasks, int nccap,
+                                                      TruncParams tp, DevStatus* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* __restrict__ Mw = reinterpret_cast<T*>(smem_raw);
+  __shared__ T sig_s[512];
+  __shared__ int perm[512];
+  __shared__ int rank_s;
+  __shared__ T hh_scratch[520];
+  const JacobiTask<T>& tk = tasks[blockIdx.x];
+  int nr, nc, k1 = 0, k2 = 0;
+  if (tk.load == 1) {
+    k1 = eff(tk.k1);
+    k2 = eff(tk.k2);
+    nr = nc = k1 + k2;
+  } else {
+    nr = eff(tk.nr);
+    nc = eff(tk.nc);
+  }
+  const int n = nc + (nc & 1);
+  const int ncc = nccap + (nccap & 1);
+  constexpr int rows_pad = G * RMAX;
+  const int ldm = jacobi_ld_g(rows_pad, (int)sizeof(T), G);
+  const int ldv = jacobi_ld(ncc, (int)sizeof(T));
+  T* __restrict__ Vw = WANT_V ? (Mw + ldm * ncc) : nullptr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int e = tid; e < rows_pad * n; e += nt) {
+    const int i = e % rows_pad, j = e / rows_pad;
+    T v = T(0);
+    if (j < nc && i < nr) {
+      if (tk.load == 0) {
+        v = tk.src[(int64_t)i * tk.rs + (int64_t)j * tk.cs];
+      } else {
+        const int ei = j, ej = i;  // element (i, j) of E^T is E[j][i]
+        if (ei < k1) {
+          if (ej < k1)
+            v = (ei == ej) ? tk.s1[ei] : T(0);
+          else {
+            T p = tk.P[(int64_t)ei * tk.ldp + (ej - k1)];
+            if (tk.P2) p += tk.P2[(int64_t)ei * tk.ldp + (ej - k1)];
+            v = p * tk.s2[ej - k1];
+          }
+        } else if (ej >= k1) {
+          v = tk.R[(int64_t)(ei - k1) * tk.ldr + (ej - k1)] * tk.s2[ej - k1];
+        }
+      }
     }
-    perm[pos] = j;
+    Mw[j * ldm + i] = v;
+  }
+  if (WANT_V)
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e % n, j = e / n;
+      Vw[j * ldv + i] = (i == j) ? T(1) : T(0);
+    }
+  if (tk.load == 1 && nr > 1) {
+    __syncthreads();
+    householder_r_transpose<T>(Mw, ldm, nr, hh_scratch);
   }
   __syncthreads();
-  if (tid == 0) {
-    int bad = 0;
-    for (int i = 0; i < nc; ++i) bad += sig_s[i] < T(0);
-    if (bad && st) atomicAdd(&st->nonfinite, 1);
-    int r = 0;
-    const double s1 = nc > 0 ? (double)sig_s[perm[0]] : 0.0;
-    if (nc > 0 && s1 > 0.0 && !bad) {
-      int numerical = 0;
-      for (int i = 0; i < nc; ++i) numerical += (double)sig_s[perm[i]] > tp.rank_tol * s1;
-      if (tp.mode == 0) {
-        r = (int)tp.param;
-      } else if (tp.mode == 1) {
-        r = 0;
-        for (int i = 0; i < nc; ++i) r += (double)sig_s[perm[i]] >= tp.param * s1;
-      } else {
-        double total = 0.0;
-        if (tk.energy) {
-          total = (double)*tk.energy;
-        } else if (tk.load == 1) {
-          for (int i = 0; i < k1; ++i) total += (double)tk.s1[i] * (double)tk.s1[i];
-          for (int i = 0; i < k2; ++i) total += (double)tk.s2[i] * (double)tk.s2[i];
-        } else {
-          for (int i = 0; i < nc; ++i) total += (double)sig_s[i] * (double)sig_s[i];
+
+  const int ngroups = nt / G;
+  const int gid = tid / G, lane = tid % G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
+  const double told = 4.0 * Eps<T>::v * sqrt((double)(nr > 1 ? nr : 1));
+  const T tol2 = T(told * told);
+  const T big2 = T(told);  // (sqrt(tol))^2
+  bool converged = (n <= 1);
+  int sweep = 0;
+  for (; sweep < tp.max_sweeps && !converged; ++sweep) {
+    int big = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      for (int slot = gid; slot < n / 2; slot += ngroups) {
+        int p, q;
+        rr_pair(n, r, slot, p, q);
+        if (p >= nc || q >= nc) continue;
+        T* x = Mw + p * ldm + lane;
+        T* y = Mw + q * ldm + lane;
+        T xr[RMAX], yr[RMAX];
+        T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0), c0 = T(0), c1 = T(0);
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+          const T xv = x[t * G], yv = y[t * G];
+          xr[t] = xv;
+          yr[t] = yv;
+          if (t & 1) {
+            a1 = fma(xv, xv, a1);
+            b1 = fma(yv, yv, b1);
+            c1 = fma(xv, yv, c1);
+          } else {
+            a0 = fma(xv, xv, a0);
+            b0 = fma(yv, yv, b0);
+            c0 = fma(xv, yv, c0);
+          }
         }
-        double cum = 0.0;
-        r = nc;
-        for (int i = 0; i < nc; ++i) {
-          const double s = (double)sig_s[perm[i]];
-          cum += s * s;
-          if (cum >= tp.param * total) {
-            r = i + 1;
-            break;
+        T a = a0 + a1, b = b0 + b1, c = c0 + c1;
+#pragma unroll
+        for (int off = G >> 1; off > 0; off >>= 1) {
+          a += __shfl_xor_sync(gmask, a, off);
+          b += __shfl_xor_sync(gmask, b, off);
+          c += __shfl_xor_sync(gmask, c, off);
+        }
+        const T ab = a * b;
+        const T cc = c * c;
+        if (ab > T(0) && cc > tol2 * ab) {
+          big |= cc > big2 * ab;
+          const T zeta = (b - a) * fast_rcp(T(2) * c);
+          const T az = fabs(zeta);
+          T t;
+          if (az > T(1)) {
+            const T iz = fast_rcp(az);
+            t = fast_rcp(az * (T(1) + T(1) / rsq(T(1) + iz * iz)));
+          } else {
+            t = fast_rcp(az + T(1) / rsq(T(1) + az * az));
+          }
+          if (zeta < T(0)) t = -t;
+          const T cs = rsq(T(1) + t * t);
+          const T sn = cs * t;
+#pragma unroll
+          for (int u = 0; u < RMAX; ++u) {
+            x[u * G] = cs * xr[u] - sn * yr[u];
+            y[u * G] = sn * xr[u] + cs * yr[u];
+          }
+          if (WANT_V) {
+            T* vx = Vw + p * ldv;
+            T* vy = Vw + q * ldv;
+            for (int i = lane; i < nc; i += G) {
+              const T xv = vx[i], yv = vy[i];
+              vx[i] = cs * xv - sn * yv;
+              vy[i] = sn * xv + cs * yv;
+            }
           }
         }
       }
-      r = min(r, numerical);
-      r = min(r, tp.rank_cap);
-      r = min(r, nc);
-      r = min(r, tk.ucap);
-      if (r < 0) r = 0;
+      __syncthreads();
     }
-    rank_s = r;
-    if (tk.rank) *tk.rank = r;
+    converged = !__syncthreads_or(big);
+  }
+  if (!converged && tid == 0 && st) atomicAdd(&st->not_converged, 1);
+  if (tid == 0 && st) {
+    atomicAdd(&st->sweeps, sweep);
+    atomicAdd(&st->cores, 1);
+  }
+
+  for (int j = gid; j < nc; j += ngroups) {
+    const T* x = Mw + j * ldm;
+    T a = T(0);
+    for (int i = lane; i < nr; i += G) a += x[i] * x[i];
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(gmask, a, off);
+    if (lane == 0) sig_s[j] = isfinite(a) ? dsqrt(a) : T(-1);
   }
   __syncthreads();
-  const int r = rank_s;
-  if (tk.sig)
-    for (int c = tid; c < tk.ucap; c += nt) tk.sig[c] = (c < r) ? sig_s[perm[c]] : T(0);
-  if (tk.U) {
-    for (int e = tid; e < nr * tk.ucap; e += nt) {
-      const int i = e / tk.ucap, c = e % tk.ucap;
-      T v = T(0);
-      if (c < r) v = Mw[(int64_t)perm[c] * ldm + i] / sig_s[perm[c]];
-      tk.U[(int64_t)i * tk.ldu + c] = v;
-    }
-  }
-  if (WANT_V && tk.V) {
-    for (int e = tid; e < nc * tk.ucap; e += nt) {
-      const int i = e / tk.ucap, c = e % tk.ucap;
-      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * ldv + i] : T(0);
-    }
-  }
-}
-
-// ------------------------------------------------------------------ helpers
-// splitmix64 (Steele, Lea & Flood, 2014) as a counter-based generator, and a
-// Box-Muller transform of two of its outputs per element.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-  uint64_t z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-template <class T>
-__global__ void k_fill_gaussian(T* out, int64_t count, uint64_t seed) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)e));
-    const uint64_t b = splitmix64(seed ^ (2 * (uint64_t)e + 1));
-    const double u1 = ((double)(a >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
-    const double u2 = (double)(b >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
-    const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-    out[e] = (T)z;
-  }
-}
-
-__global__ void k_f32_to_bf16(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
-                              int64_t ldd, int64_t rows, int64_t cols) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cols, j = e % cols;
-    dst[i * ldd + j] = __float2bfloat16_rn(src[i * lds + j]);
-  }
-}
-
-template <class T>
-__device__ __forceinline__ float to_f(T x) {
-  return (float)x;
-}
-template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
-  return __bfloat162float(x);
-}
-
-// ||X_blk||_F^2 with per-thread compensated (Kahan) FP32 sums and a
-// fixed-order FP64 combination of the per-thread partials.
-template <class TA, class TO>
-__global__ void __launch_bounds__(256) k_block_energy(const EnergyTask* __restrict__ tasks,
-                                                      const MatRef* __restrict__ mats) {
-  __shared__ double part[256];
-  const EnergyTask tk = tasks[blockIdx.x];
-  const MatRef mr = mats[tk.mat];
-  const TA* A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
-  float s = 0.f, comp = 0.f;
-  const int64_t total = (int64_t)tk.h * tk.w;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    const int64_t i = e / tk.w, j = e % tk.w;
-    const float v = to_f(A[i * mr.ld + j]);
-    const float y = v * v - comp;
-    const float t = s + y;
-    comp = (t - s) - y;
-    s = t;
-  }
-  part[threadIdx.x] = (double)s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) acc += part[i];
-    *static_cast<TO*>(tk.out) = (TO)acc;
-  }
-}
-
-// One CTA per column c < rank: find the first row of largest |U[i][c]|, flip
-// the column of U and of V if that entry is negative.
-template <class T>
-__global__ void __launch_bounds__(256) k_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n,
-                                                        const int* rank) {
-  __shared__ T bv[256];
-  __shared__ int bi[256];
-  const int c = blockIdx.x;
-  if (c >= *rank) return;
-  T best = T(-1);
-  int besti = 0x7fffffff;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const T a = fabs(U[(int64_t)i * ldu + c]);
-    if (a > best || (a == best && i < besti)) {
-      best = a;
-      besti = i;
-    }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = besti;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if ((int)threadIdx.x < off) {
-      const T ob = bv[threadIdx.x + off];
-      const int oi = bi[threadIdx.x + off];
-      if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-        bv[threadIdx.x] = ob;
-        bi[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  const int imax = bi[0];
-  if (imax >= m) return;
-  const bool neg = U[(int64_t)imax * ldu + c] < T(0);
-  __syncthreads();
-  if (!neg) return;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) U[(int64_t)i * ldu + c] = -U[(int64_t)i * ldu + c];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * ldv + c] = -V[(int64_t)i * ldv + c];
-}
-
-template <class T>
-__global__ void k_rm_to_cm(const T* __restrict__ src, int64_t lds, int rows, const int* rank, int kcap,
-                           T* __restrict__ dst, int64_t ldd) {
-  const int r = min(*rank, kcap);
-  const int64_t total = (int64_t)rows * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e / rows, i = e % rows;
-    dst[c * ldd + i] = src[i * lds + c];
-  }
-}
-
-inline int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b > 152 * 32) b = 152 * 32;
-  return (int)(b < 1 ? 1 : b);
-}
-
-}  // namespace
-
-int jacobi_pair_host(int n, int r, int s, int* p, int* q) {
-  if (n < 2 || (n & 1) || r < 0 || r >= n - 1 || s < 0 || s >= n / 2) return 1;
-  rr_pair(n, r, s, *p, *q);
-  return 0;
-}
-
-template <class T>
-cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
-                        cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
-  if (kcap > 256) return cudaErrorInvalidValue;
-  const size_t bytes = (size_t)kcap * kcap * sizeof(T);
-  const int use_smem = bytes <= 200 * 1024;
-  if (use_smem && bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-  }
-  k_chol<T><<<ntasks, 256, use_smem ? bytes : 0, s>>>(tasks, kcap, st, (T)tau, use_smem);
-  return cudaGetLastError();
+  jacobi_finish<T, WANT_V>(tk, Mw, ldm, Vw, ldv, nr, nc, k1, k2, tp, st, sig_s, perm, &rank_s);
 }
 
 // Lanes per pair G and rows per lane RMAX for a launch: all pairs of a round
@@ -656,11 +1192,63 @@ static cudaError_t launch_jacobi_v(const JacobiTask<T>* tasks, int ntasks, int n
   }
 }
 
+// Shared-memory variant: lanes per pair and rows per lane from the row cap.
+static bool jacobi_sm_shape(int nrcap, int& G, int& rmax) {
+  if (nrcap <= 32) {
+    G = 8;
+    rmax = 4;
+  } else if (nrcap <= 64) {
+    G = 16;
+    rmax = 4;
+  } else if (nrcap <= 128) {
+    G = 16;
+    rmax = 8;
+  } else if (nrcap <= 256) {
+    G = 32;
+    rmax = 8;
+  } else {
+    return false;
+  }
+  return true;
+}
+
+template <class T, bool V>
+static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, TruncParams tp,
+                                   DevStatus* st, cudaStream_t s, bool* done) {
+  *done = false;
+  int G, rmax;
+  if (!jacobi_sm_shape(nrcap, G, rmax)) return cudaSuccess;
+  const int ncc = nccap + (nccap & 1);
+  const size_t bytes = ((size_t)jacobi_ld_g(G * rmax, (int)sizeof(T), G) * ncc +
+                        (V ? (size_t)jacobi_ld(ncc, (int)sizeof(T)) * ncc : 0)) *
+                       sizeof(T);
+  if (bytes > 200 * 1024) return cudaSuccess;
+  int threads = (ncc / 2) * G;
+  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : ((threads + 31) / 32) * 32);
+  auto go = [&](auto kern) -> cudaError_t {
+    if (bytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<ntasks, threads, bytes, s>>>(tasks, nccap, tp, st);
+    *done = true;
+    return cudaGetLastError();
+  };
+  if (G == 8) return go(k_jacobi_sm<T, V, 8, 4>);
+  if (G == 16 && rmax == 4) return go(k_jacobi_sm<T, V, 16, 4>);
+  if (G == 16) return go(k_jacobi_sm<T, V, 16, 8>);
+  return go(k_jacobi_sm<T, V, 32, 8>);
+}
+
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                           TruncParams tp, DevStatus* st, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   if (nccap > 512 || nrcap > 512) return cudaErrorInvalidValue;
+  bool done = false;
+  cudaError_t e = want_v ? launch_jacobi_sm<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s, &done)
+                         : launch_jacobi_sm<T, false>(tasks, ntasks, nrcap, nccap, tp, st, s, &done);
+  if (e != cudaSuccess || done) return e;
   return want_v ? launch_jacobi_v<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s)
                 : launch_jacobi_v<T, false>(tasks, ntasks, nrcap, nccap, tp, st, s);
 }
@@ -716,8 +1304,9 @@ cudaError_t launch_rowmajor_to_colmajor(const T* src, int64_t lds, int rows, con
   return cudaGetLastError();
 }
 
-template cudaError_t launch_chol<float>(const CholTask<float>*, int, int, DevStatus*, double, cudaStream_t);
-template cudaError_t launch_chol<double>(const CholTask<double>*, int, int, DevStatus*, double, cudaStream_t);
+template cudaError_t launch_chol<float>(const CholTask<float>*, int, int, DevStatus*, double, cudaStream_t, bool);
+template cudaError_t launch_chol<double>(const CholTask<double>*, int, int, DevStatus*, double, cudaStream_t,
+                                         bool);
 template cudaError_t launch_jacobi<float>(const JacobiTask<float>*, int, int, int, bool, TruncParams, DevStatus*,
                                           cudaStream_t);
 template cudaError_t launch_jacobi<double>(const JacobiTask<double>*, int, int, int, bool, TruncParams,
