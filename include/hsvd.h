@@ -63,8 +63,13 @@ typedef enum {
  * F64:        FP64 everywhere (input must be F64).
  * F32:        FP32 GEMMs (SIMT FFMA), FP32 factors and cores.
  * BF16_MIXED: input converted to / given in BF16; the input-streaming GEMMs
- *             run on BF16 tensor cores with FP32 accumulation; factors and
- *             cores in FP32. */
+ *             run on BF16 tensor cores (tcgen05, operands by TMA) with FP32
+ *             accumulation -- the sketch and power steps with the factor in
+ *             BF16, the three projections with the factor split into BF16
+ *             hi + lo; factors and cores in FP32.  The tensor-core products
+ *             need block_rows and block_cols multiples of 8 (TMA tile
+ *             origins); other block sizes run the same products on the SIMT
+ *             kernels. */
 typedef enum {
   HSVD_PREC_F64 = 0,
   HSVD_PREC_F32 = 1,
@@ -103,6 +108,7 @@ typedef struct {
   int32_t max_rank;       /* largest final rank over the batch */
   int32_t jacobi_sweeps;  /* one-sided Jacobi sweeps summed over all cores */
   int32_t jacobi_cores;   /* number of Jacobi cores solved */
+  int32_t tensor_timeouts; /* tensor-core GEMM tiles whose bounded waits ran out (results invalid) */
 } hsvd_report;
 
 typedef struct hsvd_plan_s* hsvd_plan_t;
@@ -182,7 +188,7 @@ int32_t hsvd_step_count(hsvd_plan_t plan);
 /* hsvd_step_info -- metadata of step i: its name (NUL-terminated, truncated
  * to name_len), kind (1 GEMM NN, 2 GEMM TN, 3 split-K reduction, 4
  * CholeskyQR factor/inverse, 5 Jacobi core SVD, 6 block energy, 7 sign
- * normalisation), number of tasks, the core dimension or the column count,
+ * normalisation, 8 tensor-core GEMM, 9 BF16 conversion), number of tasks, the core dimension or the column count,
  * and the algorithmic flops and bytes of the launch (GEMMs: 2MNK and one
  * read of every operand plus one write of the result; Jacobi: 22 n^3 per
  * n x n core, the paper's count for the merge core in Section 3.1).  Any

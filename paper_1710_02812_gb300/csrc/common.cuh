@@ -39,9 +39,10 @@ struct DevStatus {
   int not_converged;
   int chol_dropped;
   int nonfinite;
-  int sweeps;  // Jacobi sweeps summed over all cores
-  int cores;   // Jacobi cores solved
-  int pad[3];
+  int sweeps;       // Jacobi sweeps summed over all cores
+  int cores;        // Jacobi cores solved
+  int tc_timeouts;  // tensor-core GEMM CTAs whose bounded waits ran out
+  int pad[2];
 };
 
 // ---------------------------------------------------------------- GEMM tasks
@@ -181,6 +182,44 @@ cudaError_t launch_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, i
 template <class T>
 cudaError_t launch_rowmajor_to_colmajor(const T* src, int64_t lds, int rows, const int* rank, int kcap,
                                         T* dst, int64_t ldd, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor-core GEMM
+// D[m][n] = sum_k A[m][k] B[n][k] (+ B2) with K-major BF16 operands read by
+// TMA through tensor maps (index into the launch's map array), FP32 D.
+// Every task of a launch uses the same MMA width N = bmax (B rows past N
+// are zero in the arena); rows past M and columns past N are not stored.
+struct TcTask {
+  int amap;            // tensor map of A
+  int a_row0, a_col0;  // origin of the task's A block (a_col0 % 8 == 0)
+  int bmap;            // tensor map of the B arena
+  int b_row0;          // first arena row of B (hi part)
+  int b2_row0;         // first arena row of the lo part, or -1
+  int M, N, K;
+  float* D;
+  int64_t ldd;
+};
+struct TcItem {
+  int task, mt;  // task and 128-row tile
+};
+bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+bool tc_available();  // the driver's tensor-map encoder could be resolved
+
+// A factor B (K x N FP32, row-major, ld ldb) written as its BF16 transpose:
+// `bmax` rows of `kpad` columns at hi (and the low parts at lo, if not null).
+struct BtTask {
+  const float* B;
+  int64_t ldb;
+  int K;
+  Dim N;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  int kpad, bmax;
+};
+cudaError_t launch_make_bt(const BtTask* tasks, const int3* items, int nitems, cudaStream_t s);
+cudaError_t launch_convert_input(const void* X, bool x_is_bf16, int64_t ld, int64_t m, int64_t n, __nv_bfloat16* Xb,
+                                 int64_t ldx, __nv_bfloat16* Xt, int64_t ldxt, cudaStream_t s);
+cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int bmax, int* err,
+                           cudaStream_t s);
 
 // Host-side helpers exported for checks without a GPU.
 int jacobi_pair_host(int n, int r, int s, int* p, int* q);

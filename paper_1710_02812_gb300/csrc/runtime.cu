@@ -9,6 +9,7 @@
 // each launch covers one step of one tree level for every block, merge or
 // slab of every matrix of the batch.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -17,6 +18,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hsvd.h"
@@ -80,7 +82,14 @@ struct PlanImpl {
   MatRef* h_mats = nullptr;  // pinned
   cudaEvent_t mats_done = nullptr;
   DevStatus* d_status = nullptr;
-  std::vector<void*> conv;     // BF16 copies of FP32 inputs (mixed path)
+  bool mixed = false;    // BF16-mixed path: plan-owned BF16 copies of the inputs
+  bool use_tc = false;   // tensor-core (tcgen05 + TMA) input products
+  std::vector<void*> xb, xt;      // per matrix: BF16 X (m x ldx) and X^T (n x ldxt), in the arena
+  std::vector<int64_t> ldx, ldxt;
+  std::vector<std::array<unsigned char, 128>> tmaps;  // tensor maps (host copies)
+  void* d_tmaps = nullptr;
+  std::vector<const void*> cur_in;  // input pointers of the run being enqueued
+  std::vector<int64_t> cur_ld;
   std::vector<void*> staging;  // device copies for hsvd_run_host
   std::vector<Blob> blobs;
   std::vector<Step> steps;
@@ -102,7 +111,7 @@ struct PlanImpl {
     if (d_status) cudaFree(d_status);
     if (h_mats) cudaFreeHost(h_mats);
     if (mats_done) cudaEventDestroy(mats_done);
-    for (void* p : conv) cudaFree(p);
+    if (d_tmaps) cudaFree(d_tmaps);
     for (void* p : staging) cudaFree(p);
     for (auto& v : pending)
       for (auto e : v) cudaEventDestroy(e);
@@ -344,10 +353,33 @@ struct Builder {
   struct InputOp {
     GI g;
     bool tn;
+    // the product as asked for, for the tensor-core path
+    bool xt;
+    int mat;
+    bool vt;
+    int64_t r0, c0;
+    int h, w;
+    const T* B;
+    int64_t ldb;
+    Dim N;
+    T* C;
+    int64_t ldc;
   };
   InputOp input_op(bool xt, int mat, bool view_t, int64_t r0, int64_t c0, int h, int w, const T* B, int64_t ldb,
                    Dim N, T* C, int64_t ldc) {
     InputOp io;
+    io.xt = xt;
+    io.mat = mat;
+    io.vt = view_t;
+    io.r0 = r0;
+    io.c0 = c0;
+    io.h = h;
+    io.w = w;
+    io.B = B;
+    io.ldb = ldb;
+    io.N = N;
+    io.C = C;
+    io.ldc = ldc;
     GI& g = io.g;
     g = blank<GI>();
     g.mat = mat;
@@ -382,12 +414,103 @@ struct Builder {
     return io;
   }
 
-  void emit_input(const std::string& name, std::vector<InputOp>& ops) {
+  void emit_input(const std::string& name, std::vector<InputOp>& ops, bool lo = false) {
     if (ops.empty()) return;
+    if (P.use_tc) {
+      emit_input_tc(name, ops, lo);
+      return;
+    }
     std::vector<GI> nn_t, tn_t;
     for (auto& o : ops) (o.tn ? tn_t : nn_t).push_back(o.g);
     emit_gemm(name, nn_t, false);
     emit_gemm(name, tn_t, true);
+  }
+
+  int nmaps = 0;  // tensor maps created so far (same count in both passes)
+  int add_map(const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    if (base_real()) {
+      std::array<unsigned char, 128> m;
+      if (!make_tmap_bf16(m.data(), base, rows, cols, ld, box_rows)) map_failed = true;
+      P.tmaps.push_back(m);
+    }
+    return nmaps++;
+  }
+  bool map_failed = false;
+  bool base_real() const { return base != nullptr; }
+
+  // Tensor-core products: every op's factor B (K x N FP32) is written as its
+  // BF16 transpose (hi, and lo when `lo`) into a step arena, then one
+  // tcgen05 launch computes C = op(X_blk) B for all ops.  op = identity reads
+  // the view matrix at (r0, c0); op = transpose reads the transposed copy at
+  // (c0, r0), so both operands are K-major.
+  void emit_input_tc(const std::string& name, const std::vector<InputOp>& ops, bool lo) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return;  // only the FP32-factor (mixed) path has tensor-core products
+    } else {
+      emit_input_tc_f32(name, ops, lo);
+    }
+  }
+  void emit_input_tc_f32(const std::string& name, const std::vector<InputOp>& ops, bool lo) {
+    int bmax = 16, kmax = 1;
+    for (const auto& o : ops) {
+      bmax = std::max(bmax, ((o.N.cap + 15) / 16) * 16);
+      kmax = std::max(kmax, o.xt ? o.h : o.w);
+    }
+    const int kpad = ((kmax + 63) / 64) * 64;
+    const int per = lo ? 2 : 1;
+    __nv_bfloat16* arena = alloc<__nv_bfloat16>((size_t)ops.size() * per * bmax * kpad);
+    const int bmap = add_map(arena, (int64_t)ops.size() * per * bmax, kpad, kpad, bmax);
+    std::vector<BtTask> bt;
+    std::vector<int3> bti;
+    std::vector<TcTask> tc;
+    std::vector<TcItem> tci;
+    double flops = 0, bytes = 0;
+    for (size_t t = 0; t < ops.size(); ++t) {
+      const InputOp& o = ops[t];
+      const int M = o.xt ? o.w : o.h, K = o.xt ? o.h : o.w;
+      BtTask b;
+      b.B = reinterpret_cast<const float*>(o.B);
+      b.ldb = o.ldb;
+      b.K = K;
+      b.N = o.N;
+      b.hi = arena + (size_t)t * per * bmax * kpad;
+      b.lo = lo ? b.hi + (size_t)bmax * kpad : nullptr;
+      b.kpad = kpad;
+      b.bmax = bmax;
+      bt.push_back(b);
+      for (int nt = 0; nt < bmax / 32 + (bmax % 32 ? 1 : 0); ++nt)
+        for (int kt = 0; kt < kpad / 32; ++kt) bti.push_back(make_int3((int)t, nt, kt));
+      // the view matrix is X (or X^T when the tree is transposed)
+      const bool use_xt = o.xt != o.vt;  // read the stored X^T copy
+      TcTask k;
+      k.amap = 2 * o.mat + (use_xt ? 1 : 0);
+      k.a_row0 = (int)(o.xt ? o.c0 : o.r0);
+      k.a_col0 = (int)(o.xt ? o.r0 : o.c0);
+      k.bmap = bmap;
+      k.b_row0 = (int)(t * per * bmax);
+      k.b2_row0 = lo ? k.b_row0 + bmax : -1;
+      k.M = M;
+      k.N = o.N.cap;
+      k.K = K;
+      k.D = reinterpret_cast<float*>(o.C);
+      k.ldd = o.ldc;
+      tc.push_back(k);
+      for (int mt = 0; mt < (M + 127) / 128; ++mt) tci.push_back(TcItem{(int)t, mt});
+      flops += 2.0 * M * o.N.cap * K;
+      bytes += (double)M * K * 2 + (double)o.N.cap * K * 2 * per + (double)M * o.N.cap * 4;
+    }
+    PlanImpl* p = &P;
+    const size_t b1 = P.add_blob(bt), b2 = P.add_blob(bti), b3 = P.add_blob(tc), b4 = P.add_blob(tci);
+    const int n2 = (int)bti.size(), n4 = (int)tci.size();
+    P.steps.push_back(Step{name + ".bt", [p, b1, b2, n2](cudaStream_t s) {
+                             return launch_make_bt(p->table<BtTask>(b1), p->table<int3>(b2), n2, s);
+                           }});
+    tag(9, (int)ops.size(), bmax, 0, (double)ops.size() * bmax * kpad * 2 * per);
+    P.steps.push_back(Step{name, [p, b3, b4, n4, bmax](cudaStream_t s) {
+                             return launch_tc_gemm(p->d_tmaps, p->table<TcTask>(b3), p->table<TcItem>(b4), n4, bmax,
+                                                   &p->d_status->tc_timeouts, s);
+                           }});
+    tag(8, (int)ops.size(), bmax, flops, bytes);
   }
 
   // -------------------------------------------------------------- small steps
@@ -678,6 +801,42 @@ struct Builder {
                                   }});
     }
 
+    // ---------------------------------------------------- a1: BF16 copies
+    // The mixed path reads the input as BF16 (X, and X^T for the tensor-core
+    // products); the copies are converted from the caller's matrices at the
+    // start of every run.
+    if (P.mixed) {
+      P.xb.assign(P.batch, nullptr);
+      P.xt.assign(P.batch, nullptr);
+      P.ldx.assign(P.batch, 0);
+      P.ldxt.assign(P.batch, 0);
+      for (int b = 0; b < P.batch; ++b) {
+        P.ldx[b] = ((P.n[b] + 7) / 8) * 8;
+        P.xb[b] = alloc<__nv_bfloat16>((size_t)P.m[b] * P.ldx[b]);
+        if (P.use_tc) {
+          P.ldxt[b] = ((P.m[b] + 7) / 8) * 8;
+          P.xt[b] = alloc<__nv_bfloat16>((size_t)P.n[b] * P.ldxt[b]);
+          add_map(P.xb[b], P.m[b], P.n[b], P.ldx[b], 128);
+          add_map(P.xt[b], P.n[b], P.m[b], P.ldxt[b], 128);
+        }
+      }
+      PlanImpl* p = &P;
+      P.steps.push_back(Step{"convert.input", [p](cudaStream_t s) {
+                               const bool bf = p->in_dtype == HSVD_DTYPE_BF16;
+                               for (int b = 0; b < p->batch; ++b) {
+                                 cudaError_t e = launch_convert_input(
+                                     p->cur_in[b], bf, p->cur_ld[b], p->m[b], p->n[b],
+                                     static_cast<__nv_bfloat16*>(p->xb[b]), p->ldx[b],
+                                     static_cast<__nv_bfloat16*>(p->xt[b]), p->ldxt[b], s);
+                                 if (e != cudaSuccess) return e;
+                               }
+                               return cudaSuccess;
+                             }});
+      double by = 0;
+      for (int b = 0; b < P.batch; ++b) by += (double)P.m[b] * P.n[b] * (P.in_elem + (P.use_tc ? 4 : 2));
+      tag(9, P.batch, 0, 0, by);
+    }
+
     // ---------------------------------------------------- level 0: blocks
     std::vector<BlockW> bw;
     std::vector<std::vector<std::vector<Factor>>> slab_leaves(P.batch);
@@ -763,7 +922,7 @@ struct Builder {
       std::vector<InputOp> ops;
       for (auto& w : bw)
         ops.push_back(input_op(true, w.mat, w.vt, w.r0, w.c0, w.h, w.w, w.Q, w.kpb, dimc(w.kpb), w.Wm, w.kpb));
-      emit_input("block.project", ops);
+      emit_input("block.project", ops, true);
       emit_orth("block.orthR", orth_list(2), 2, kp);
       std::vector<JacobiTask<T>> jt;
       std::vector<GS> ut;
@@ -839,7 +998,7 @@ struct Builder {
         vt_gemm.push_back(nn_(Qz, kc, nn, kj, UR, kc, dimd(kc, out.rank), out.U, kc));
         row_lists[b].push_back(out);
       }
-      emit_input("slab.project", ops);
+      emit_input("slab.project", ops, true);
       emit_orth("slab.orth", ow, 2, kc);
       emit_jacobi("slab.core", jt, kc, kc, false, tp);
       emit_gemm("slab.V", vt_gemm, false);
@@ -900,7 +1059,7 @@ struct Builder {
         ug.push_back(nn_(Qy, kc, mm, kv, UR, kc, dimd(kc, rf), Uf, kc));
         vg.push_back(nn_(V.U, kc, nn, kv, WR, kc, dimd(kc, rf), Vf, kc));
       }
-      emit_input("final.project", ops);
+      emit_input("final.project", ops, true);
       emit_orth("final.orth", ow, 2, kc);
       emit_jacobi("final.core", jt, kc, kc, true, tpf);
       emit_gemm("final.U", ug, false);
@@ -936,6 +1095,7 @@ hsvd_status build_plan(PlanImpl& P) {
   P.init_steps.clear();
   P.blobs.clear();
   P.outs.clear();
+  P.tmaps.clear();
   if (cudaMalloc(&P.arena, std::max<size_t>(P.arena_bytes, 256)) != cudaSuccess) {
     P.arena = nullptr;
     cudaGetLastError();
@@ -944,6 +1104,16 @@ hsvd_status build_plan(PlanImpl& P) {
   Builder<T, TA> real(P, P.arena);
   real.build();
   if (real.off != P.arena_bytes) return HSVD_ECUDA;  // layout must be identical
+  if (real.map_failed) return HSVD_EUNSUPPORTED;
+  if (!P.tmaps.empty()) {
+    if (cudaMalloc(&P.d_tmaps, P.tmaps.size() * 128) != cudaSuccess) {
+      P.d_tmaps = nullptr;
+      cudaGetLastError();
+      return HSVD_ENOMEM;
+    }
+    if (cudaMemcpy(P.d_tmaps, P.tmaps.data(), P.tmaps.size() * 128, cudaMemcpyHostToDevice) != cudaSuccess)
+      return HSVD_ECUDA;
+  }
   size_t total = 0;
   for (auto& b : P.blobs) {
     b.dev_off = total;
@@ -1096,16 +1266,12 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   }
   if (cudaEventCreateWithFlags(&P.mats_done, cudaEventDisableTiming) != cudaSuccess) return HSVD_ECUDA;
   if (cudaMemset(P.d_status, 0, sizeof(hsvd::DevStatus)) != cudaSuccess) return HSVD_ECUDA;
-  if (prec == HSVD_PREC_BF16_MIXED && in_dtype == HSVD_DTYPE_F32) {
-    for (int b = 0; b < batch; ++b) {
-      void* p = nullptr;
-      if (cudaMalloc(&p, (size_t)m[b] * n[b] * 2) != cudaSuccess) {
-        cudaGetLastError();
-        return HSVD_ENOMEM;
-      }
-      P.conv.push_back(p);
-    }
-  }
+  P.mixed = prec == HSVD_PREC_BF16_MIXED;
+  // Tensor-core products need the block origins on 8-element (16-byte)
+  // boundaries for TMA, a sketch of at most 256 columns, and the tensor-map
+  // encoder of the driver.
+  P.use_tc = P.mixed && block_rows % 8 == 0 && block_cols % 8 == 0 && P.kp <= 256 && !std::getenv("HSVD_NO_TC") &&
+             hsvd::tc_available();
   if (P.host_staging) {
     for (int b = 0; b < batch; ++b) {
       void* p = nullptr;
@@ -1131,11 +1297,12 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
 static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_t* lda, cudaStream_t s) {
   PlanImpl& P = plan->impl;
   if (cudaEventSynchronize(P.mats_done) != cudaSuccess) return HSVD_ECUDA;
-  const bool conv = !P.conv.empty();
+  P.cur_in.assign(A, A + P.batch);
+  P.cur_ld.assign(lda, lda + P.batch);
   for (int b = 0; b < P.batch; ++b) {
-    if (conv) {
-      P.h_mats[b].ptr = P.conv[b];
-      P.h_mats[b].ld = P.n[b];
+    if (P.mixed) {
+      P.h_mats[b].ptr = P.xb[b];
+      P.h_mats[b].ld = P.ldx[b];
     } else {
       P.h_mats[b].ptr = A[b];
       P.h_mats[b].ld = lda[b];
@@ -1146,11 +1313,6 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
     return HSVD_ECUDA;
   if (cudaEventRecord(P.mats_done, s) != cudaSuccess) return HSVD_ECUDA;
   if (cudaMemsetAsync(P.d_status, 0, sizeof(hsvd::DevStatus), s) != cudaSuccess) return HSVD_ECUDA;
-  if (conv)
-    for (int b = 0; b < P.batch; ++b)
-      if (hsvd::launch_f32_to_bf16(static_cast<const float*>(A[b]), lda[b], static_cast<__nv_bfloat16*>(P.conv[b]),
-                                   P.n[b], P.m[b], P.n[b], s) != cudaSuccess)
-        return HSVD_ECUDA;
   const bool trace = std::getenv("HSVD_TRACE") != nullptr;
   const bool timed = P.timing || trace;
   std::vector<cudaEvent_t> ev;
@@ -1342,7 +1504,7 @@ int64_t hsvd_workspace_bytes(hsvd_plan_t plan) {
   if (!plan) return 0;
   const PlanImpl& P = plan->impl;
   int64_t t = (int64_t)P.arena_bytes + (int64_t)P.tables_bytes;
-  for (size_t b = 0; b < P.conv.size(); ++b) t += P.m[b] * P.n[b] * 2;
+  if (P.d_tmaps) t += (int64_t)P.tmaps.size() * 128;
   for (size_t b = 0; b < P.staging.size(); ++b) t += P.m[b] * P.n[b] * (int64_t)P.in_elem;
   return t;
 }
@@ -1350,7 +1512,7 @@ int64_t hsvd_workspace_bytes(hsvd_plan_t plan) {
 int32_t hsvd_launches_per_run(hsvd_plan_t plan) {
   if (!plan) return -1;
   const PlanImpl& P = plan->impl;
-  return P.launches_per_run + (P.conv.empty() ? 0 : P.batch);
+  return P.launches_per_run;
 }
 
 int32_t hsvd_step_count(hsvd_plan_t plan) {

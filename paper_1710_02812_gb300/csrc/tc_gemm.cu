@@ -1,0 +1,329 @@
+// Tensor-core GEMM for the input-streaming products of the BF16-mixed path:
+//   D[m][n] = sum_k A[m][k] * B[n][k]  (+ sum_k A[m][k] * B2[n][k])
+// with A and B both K-major BF16 (A: a block of the BF16 input X or of its
+// transposed copy; B: the transposed BF16 copy of a factor, zero beyond the
+// task's K), D FP32 row-major.  The optional second B carries the low BF16
+// part of a factor split hi + lo, accumulated into the same tensor-memory
+// accumulator, which gives the projections near-FP32 accuracy.
+//
+// One CTA computes one 128-row tile of one task for all N (<= 256) columns:
+//   warp 0, one thread : TMA loads of the A / B tiles (128B swizzle) into a
+//                        ring of stages, completion on "full" mbarriers;
+//   warp 1, one thread : tcgen05.mma (kind::f16, M = 128, N = Nmma, K = 16
+//                        per instruction) into TMEM; tcgen05.commit frees a
+//                        stage ("empty") and finally signals "done";
+//   warps 0-3          : tcgen05.ld of their 32 TMEM lanes, FP32 stores.
+// Every wait is bounded: on timeout the CTA raises an error flag, waits for
+// its own copies and MMAs (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace hsvd {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;  // 64 BF16 = one 128-byte swizzle row
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile stored as rows of 128
+// bytes with the 128-byte swizzle (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B): start address >> 4 (bits 0-13), leading byte
+// offset 16 >> 4 (unused for this layout), stride byte offset 1024 >> 4
+// between groups of 8 rows (bits 32-45), descriptor version 1 (bit 46),
+// layout type 2 = 128-byte swizzle (bits 61-63).  Tiles are 1024-byte
+// aligned, so the base offset (bits 49-51) is 0; advancing along K inside
+// the swizzle row adds the byte offset to the start address.
+__device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(16 >> 4) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits
+// 7-9 = 1), B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one per lane).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restrict__ maps,
+                                                    const TcTask* __restrict__ tasks,
+                                                    const TcItem* __restrict__ items, int stages, int bmax,
+                                                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[8];
+  __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+
+  const TcItem it = items[blockIdx.x];
+  const TcTask tk = tasks[it.task];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool has_lo = tk.b2_row0 >= 0;
+  const int nk = (tk.K + TC_BK - 1) / TC_BK;
+  const uint32_t a_bytes = TC_BM * TC_BK * 2;
+  const uint32_t b_bytes = static_cast<uint32_t>(bmax) * TC_BK * 2;
+  const uint32_t stage_bytes = a_bytes + 2u * b_bytes;
+  const uint32_t ncols = bmax <= 32 ? 32 : bmax <= 64 ? 64 : bmax <= 128 ? 128 : 256;
+  // 1024-byte aligned ring of stages: [A | B | B2]
+  const uint32_t base_s = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* base = smem_raw + (base_s - smem_u32(smem_raw));
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base;
+  const CUtensorMap* amap = maps + tk.amap;
+  const CUtensorMap* bmap = maps + tk.bmap;
+  const int arow = tk.a_row0 + it.mt * TC_BM;
+
+  int issued = 0;   // producer: tiles issued
+  int mma_done = 0; // issuer: stages committed
+  if (warp == 0 && lane == 0) {
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % stages;
+      if (kt >= stages && !mbar_wait(&empty_bar[s], ((kt / stages) - 1) & 1)) {
+        atomicExch(&failed, 1);
+        break;
+      }
+      if (*(volatile int*)&failed) break;
+      unsigned char* st = base + s * stage_bytes;
+      mbar_arrive_expect_tx(&full_bar[s], a_bytes + (has_lo ? 2u : 1u) * b_bytes);
+      tma_load_2d(st, amap, &full_bar[s], tk.a_col0 + kt * TC_BK, arow);
+      tma_load_2d(st + a_bytes, bmap, &full_bar[s], kt * TC_BK, tk.b_row0);
+      if (has_lo) tma_load_2d(st + a_bytes + b_bytes, bmap, &full_bar[s], kt * TC_BK, tk.b2_row0);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_f32(TC_BM, bmax);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % stages;
+      if (!mbar_wait(&full_bar[s], (kt / stages) & 1)) {
+        atomicExch(&failed, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = base_s + s * stage_bytes;
+      const uint32_t sb = sa + a_bytes;
+      const uint32_t sb2 = sb + b_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint64_t ad = desc_k_sw128(sa + kk * 32);
+        umma_bf16(tacc, ad, desc_k_sw128(sb + kk * 32), idesc, (kt | kk) != 0);
+        if (has_lo) umma_bf16(tacc, ad, desc_k_sw128(sb2 + kk * 32), idesc, 1u);
+      }
+      umma_commit(&empty_bar[s]);
+      ++mma_done;
+    }
+    umma_commit(&done_bar);
+  }
+  __syncthreads();
+
+  // epilogue: wait for the accumulator, then each warp reads its 32 lanes
+  bool ok = !*(volatile int*)&failed;
+  if (ok) ok = mbar_wait(&done_bar, 0);
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(&failed, 1);
+      atomicOr(err, 1);
+    }
+    // let in-flight copies and MMAs land before the shared memory and the
+    // tensor memory are released (bounded again)
+    if (warp == 0 && lane == 0)
+      for (int t = issued > stages ? issued - stages : 0; t < issued; ++t)
+        mbar_wait(&full_bar[t % stages], (t / stages) & 1);
+    if (tid == 32) mbar_wait(&done_bar, 0);
+  } else {
+    tc_fence_after();
+    const int row = warp * 32 + lane;
+    const int gm = it.mt * TC_BM + row;
+    float v[32];
+    for (int c0 = 0; c0 < bmax; c0 += 32) {
+      tmem_ld32(tacc + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
+      if (gm < tk.M) {
+        float* drow = tk.D + static_cast<int64_t>(gm) * tk.ldd;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (c0 + i < tk.N) drow[c0 + i] = v[i];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tacc, ncols);
+  (void)mma_done;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+}  // namespace
+
+// Tensor map of a K-major BF16 matrix (rows x cols, leading dimension ld
+// elements) read in boxes of box_rows x 64 with the 128-byte swizzle.  The
+// base must be 16-byte aligned and ld a multiple of 8 (checked by the
+// encoder); out-of-range boxes read zeros.
+bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || box_rows < 1 || box_rows > 256) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(out128), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+size_t tc_smem_bytes(int stages, int bmax) {
+  return static_cast<size_t>(stages) * (TC_BM * TC_BK * 2 + 2 * static_cast<size_t>(bmax) * TC_BK * 2) + 1024;
+}
+
+int tc_stages(int bmax) {
+  int st = 4;
+  while (st > 2 && tc_smem_bytes(st, bmax) > 200 * 1024) --st;
+  return st;
+}
+
+cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int bmax,
+                           int* err, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (bmax < 16 || bmax > 256 || (bmax & 15)) return cudaErrorInvalidValue;
+  const int stages = tc_stages(bmax);
+  const size_t bytes = tc_smem_bytes(stages, bmax);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_tc_gemm<<<nitems, 128, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, stages, bmax, err);
+  return cudaGetLastError();
+}
+
+}  // namespace hsvd

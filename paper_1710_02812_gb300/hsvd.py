@@ -27,7 +27,8 @@ EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
             "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc")
-STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs"}
+STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
+             8: "gemm_tc", 9: "convert"}
 
 
 class HsvdError(RuntimeError):
@@ -46,7 +47,7 @@ class Report(ctypes.Structure):
     _fields_ = [("not_converged", ctypes.c_int32), ("chol_dropped", ctypes.c_int32),
                 ("nonfinite", ctypes.c_int32), ("min_rank", ctypes.c_int32),
                 ("max_rank", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
-                ("jacobi_cores", ctypes.c_int32)]
+                ("jacobi_cores", ctypes.c_int32), ("tensor_timeouts", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -260,3 +260,46 @@ def test_nonfinite_input_is_reported():
     x[17, 33] = np.nan
     (_,), st, _ = run_gpu([x], 64, 64, "fixed_k", 8, "f32")
     assert st["nonfinite"] > 0
+
+
+# ---------------------------------------------------------------- mixed, tensor cores
+
+@pytest.mark.parametrize("m,n,br,bc,k", [
+    (700, 900, 256, 192, 24),    # ragged 128-row tiles and K tails through the tcgen05 path
+    (2048, 1536, 512, 512, 64),  # full 128-wide sketch
+])
+def test_bf16_mixed_tensor_core_ragged(m, n, br, bc, k):
+    r = min(m, n, 300)
+    xb = W.bf16_round(W.exp_decay(m, n, r=r, noise=1e-5, tag=m + 3 * n, dtype=np.float32))
+    (got,), st, _ = run_gpu([xb], br, bc, "fixed_k", k, "bf16_mixed")
+    assert st["tensor_timeouts"] == 0
+    ref = oracle_run(xb, br, bc, "fixed_k", k, "bf16_mixed")
+    check(xb, got, ref, "bf16_mixed", f"tc {m}x{n}", s_true=np.exp(-np.arange(r) / 20.0))
+
+
+def test_bf16_mixed_bf16_input_dtype():
+    """BF16 storage given directly (in_dtype bf16) reads the same values."""
+    xb = W.bf16_round(W.exp_decay(768, 640, r=200, noise=1e-5, tag=71, dtype=np.float32))
+    # an exp(-i/20) spectrum needs ~48 extra sketch columns for a 0.1 gap at k
+    plan = hsvd.Plan(768, 640, 128, 128, "fixed_k", 16, prec="bf16_mixed", in_dtype="bf16", oversample=48)
+    t = torch.from_numpy(xb).cuda().to(torch.bfloat16)
+    plan.run([t])
+    got = plan.factors(0)
+    ref = oracle_run(xb, 128, 128, "fixed_k", 16, "bf16_mixed")
+    check(xb, got, ref, "bf16_mixed", "bf16 input", s_true=np.exp(-np.arange(200) / 20.0))
+
+
+def test_bf16_mixed_simt_fallback_for_unaligned_blocks():
+    """Block origins off 8-element boundaries cannot be TMA tile origins:
+    the mixed path then runs its products on the SIMT kernels."""
+    xb = W.bf16_round(W.exp_decay(600, 500, r=150, noise=1e-5, tag=72, dtype=np.float32))
+    (got,), st, _ = run_gpu([xb], 250, 190, "fixed_k", 16, "bf16_mixed", oversample=48)
+    ref = oracle_run(xb, 250, 190, "fixed_k", 16, "bf16_mixed")
+    check(xb, got, ref, "bf16_mixed", "simt fallback", s_true=np.exp(-np.arange(150) / 20.0))
+
+
+def test_bf16_mixed_row_then_col_tensor_core():
+    xb = W.bf16_round(W.exp_decay(640, 1024, r=200, noise=1e-5, tag=73, dtype=np.float32))
+    (got,), st, _ = run_gpu([xb], 128, 256, "fixed_k", 20, "bf16_mixed", tree="row_then_col", oversample=48)
+    ref = oracle_run(xb, 128, 256, "fixed_k", 20, "bf16_mixed", tree="row_then_col")
+    check(xb, got, ref, "bf16_mixed", "tc row_then_col", s_true=np.exp(-np.arange(200) / 20.0))
