@@ -1074,15 +1074,37 @@ __global__ void __launch_bounds__(1024, 1) k_jacobi_sm(const JacobiTask<T>* __re
         int p, q;
         rr_pair(n, r, slot, p, q);
         if (p >= nc || q >= nc) continue;
-        T* x = Mw + p * ldm + lane;
-        T* y = Mw + q * ldm + lane;
+        // lane l holds rows 4l..4l+3 of every chunk of 4G rows (128-bit
+        // shared-memory accesses: a quarter of the load/store instructions)
         T xr[RMAX], yr[RMAX];
         T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0), c0 = T(0), c1 = T(0);
+        if constexpr (sizeof(T) == 4) {
+          const float4* x4 = reinterpret_cast<const float4*>(Mw + p * ldm) + lane;
+          const float4* y4 = reinterpret_cast<const float4*>(Mw + q * ldm) + lane;
+#pragma unroll
+          for (int t = 0; t < RMAX / 4; ++t) {
+            const float4 xv = x4[t * G], yv = y4[t * G];
+            xr[4 * t] = xv.x;
+            xr[4 * t + 1] = xv.y;
+            xr[4 * t + 2] = xv.z;
+            xr[4 * t + 3] = xv.w;
+            yr[4 * t] = yv.x;
+            yr[4 * t + 1] = yv.y;
+            yr[4 * t + 2] = yv.z;
+            yr[4 * t + 3] = yv.w;
+          }
+        } else {
+          const T* x = Mw + p * ldm + lane;
+          const T* y = Mw + q * ldm + lane;
+#pragma unroll
+          for (int t = 0; t < RMAX; ++t) {
+            xr[t] = x[t * G];
+            yr[t] = y[t * G];
+          }
+        }
 #pragma unroll
         for (int t = 0; t < RMAX; ++t) {
-          const T xv = x[t * G], yv = y[t * G];
-          xr[t] = xv;
-          yr[t] = yv;
+          const T xv = xr[t], yv = yr[t];
           if (t & 1) {
             a1 = fma(xv, xv, a1);
             b1 = fma(yv, yv, b1);
@@ -1104,22 +1126,45 @@ __global__ void __launch_bounds__(1024, 1) k_jacobi_sm(const JacobiTask<T>* __re
         const T cc = c * c;
         if (ab > T(0) && cc > tol2 * ab) {
           big |= cc > big2 * ab;
+          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with sqrt(x) = x rsqrt(x);
+          // for |zeta| > 1e18 (zeta^2 would overflow) t = 1 / (2 zeta).
           const T zeta = (b - a) * fast_rcp(T(2) * c);
           const T az = fabs(zeta);
           T t;
-          if (az > T(1)) {
-            const T iz = fast_rcp(az);
-            t = fast_rcp(az * (T(1) + T(1) / rsq(T(1) + iz * iz)));
+          if (az < T(1e18)) {
+            const T q1 = T(1) + az * az;
+            t = fast_rcp(az + q1 * rsq(q1));
           } else {
-            t = fast_rcp(az + T(1) / rsq(T(1) + az * az));
+            t = T(0.5) * fast_rcp(az);
           }
           if (zeta < T(0)) t = -t;
           const T cs = rsq(T(1) + t * t);
           const T sn = cs * t;
+          if constexpr (sizeof(T) == 4) {
+            float4* x4 = reinterpret_cast<float4*>(Mw + p * ldm) + lane;
+            float4* y4 = reinterpret_cast<float4*>(Mw + q * ldm) + lane;
 #pragma unroll
-          for (int u = 0; u < RMAX; ++u) {
-            x[u * G] = cs * xr[u] - sn * yr[u];
-            y[u * G] = sn * xr[u] + cs * yr[u];
+            for (int u = 0; u < RMAX / 4; ++u) {
+              float4 xo, yo;
+              xo.x = cs * xr[4 * u] - sn * yr[4 * u];
+              xo.y = cs * xr[4 * u + 1] - sn * yr[4 * u + 1];
+              xo.z = cs * xr[4 * u + 2] - sn * yr[4 * u + 2];
+              xo.w = cs * xr[4 * u + 3] - sn * yr[4 * u + 3];
+              yo.x = sn * xr[4 * u] + cs * yr[4 * u];
+              yo.y = sn * xr[4 * u + 1] + cs * yr[4 * u + 1];
+              yo.z = sn * xr[4 * u + 2] + cs * yr[4 * u + 2];
+              yo.w = sn * xr[4 * u + 3] + cs * yr[4 * u + 3];
+              x4[u * G] = xo;
+              y4[u * G] = yo;
+            }
+          } else {
+            T* x = Mw + p * ldm + lane;
+            T* y = Mw + q * ldm + lane;
+#pragma unroll
+            for (int u = 0; u < RMAX; ++u) {
+              x[u * G] = cs * xr[u] - sn * yr[u];
+              y[u * G] = sn * xr[u] + cs * yr[u];
+            }
           }
           if (WANT_V) {
             T* vx = Vw + p * ldv;

@@ -248,10 +248,15 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
     for (int c0 = 0; c0 < bmax; c0 += 32) {
       tmem_ld32(tacc + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
       if (gm < tk.M) {
-        float* drow = tk.D + static_cast<int64_t>(gm) * tk.ldd;
+        float* drow = tk.D + static_cast<int64_t>(gm) * tk.ldd + c0;
+        if (c0 + 32 <= tk.N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (c0 + i < tk.N) drow[c0 + i] = v[i];
+          for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(drow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < tk.N) drow[i] = v[i];
+        }
       }
     }
   }
