@@ -15,6 +15,8 @@
 //               energies, sign normalisation and layout conversion.
 #include <math.h>
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace hsvd {
@@ -999,7 +1001,7 @@ __global__ void __launch_bounds__(512, JacobiOcc<T, RMAX>::value) k_jacobi(const
 // cyclic method converges quadratically, so the off-diagonal left behind is
 // below tol and the verification sweep is skipped.
 template <class T, bool WANT_V, int G, int RMAX>
-__global__ void __launch_bounds__(1024, 1) k_jacobi_sm(const JacobiTask<T>* __restrict__ tasks, int nccap,
+__global__ void __launch_bounds__(RMAX >= 16 ? 512 : 1024, 1) k_jacobi_sm(const JacobiTask<T>* __restrict__ tasks, int nccap,
                                                       TruncParams tp, DevStatus* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* __restrict__ Mw = reinterpret_cast<T*>(smem_raw);
@@ -1239,22 +1241,24 @@ static cudaError_t launch_jacobi_v(const JacobiTask<T>* tasks, int ntasks, int n
 
 // Shared-memory variant: lanes per pair and rows per lane from the row cap.
 static bool jacobi_sm_shape(int nrcap, int& G, int& rmax) {
-  if (nrcap <= 32) {
-    G = 8;
+  // Lanes per pair: fewer lanes mean less replicated rotation arithmetic and
+  // shorter shuffle reductions, more lanes more warps to hide latency.
+  // HSVD_JACOBI_LANES (4, 8 or 16) overrides the default of 8 for tuning.
+  static int lanes = [] {
+    const char* e = std::getenv("HSVD_JACOBI_LANES");
+    const int v = e ? std::atoi(e) : 8;
+    return (v == 4 || v == 8 || v == 16) ? v : 8;
+  }();
+  if (nrcap > 256) return false;
+  const int rows = nrcap <= 32 ? 32 : nrcap <= 64 ? 64 : nrcap <= 128 ? 128 : 256;
+  G = lanes;
+  while (rows / G > 32) G *= 2;  // at most 32 rows per lane
+  rmax = rows / G;
+  if (rmax < 4) {
     rmax = 4;
-  } else if (nrcap <= 64) {
-    G = 16;
-    rmax = 4;
-  } else if (nrcap <= 128) {
-    G = 16;
-    rmax = 8;
-  } else if (nrcap <= 256) {
-    G = 32;
-    rmax = 8;
-  } else {
-    return false;
+    G = rows / 4;
   }
-  return true;
+  return G <= 32;
 }
 
 template <class T, bool V>
@@ -1269,7 +1273,8 @@ static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int 
                        sizeof(T);
   if (bytes > 200 * 1024) return cudaSuccess;
   int threads = (ncc / 2) * G;
-  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : ((threads + 31) / 32) * 32);
+  const int tmax = rmax >= 16 ? 512 : 1024;  // the kernel's launch bound
+  threads = threads < 32 ? 32 : (threads > tmax ? tmax : ((threads + 31) / 32) * 32);
   auto go = [&](auto kern) -> cudaError_t {
     if (bytes > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1279,10 +1284,20 @@ static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int 
     *done = true;
     return cudaGetLastError();
   };
-  if (G == 8) return go(k_jacobi_sm<T, V, 8, 4>);
-  if (G == 16 && rmax == 4) return go(k_jacobi_sm<T, V, 16, 4>);
-  if (G == 16) return go(k_jacobi_sm<T, V, 16, 8>);
-  return go(k_jacobi_sm<T, V, 32, 8>);
+  switch (G * 100 + rmax) {
+    case 404: return go(k_jacobi_sm<T, V, 4, 4>);
+    case 408: return go(k_jacobi_sm<T, V, 4, 8>);
+    case 416: return go(k_jacobi_sm<T, V, 4, 16>);
+    case 432: return go(k_jacobi_sm<T, V, 4, 32>);
+    case 804: return go(k_jacobi_sm<T, V, 8, 4>);
+    case 808: return go(k_jacobi_sm<T, V, 8, 8>);
+    case 816: return go(k_jacobi_sm<T, V, 8, 16>);
+    case 832: return go(k_jacobi_sm<T, V, 8, 32>);
+    case 1604: return go(k_jacobi_sm<T, V, 16, 4>);
+    case 1608: return go(k_jacobi_sm<T, V, 16, 8>);
+    case 1616: return go(k_jacobi_sm<T, V, 16, 16>);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class T>
