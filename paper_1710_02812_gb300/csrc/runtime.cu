@@ -28,7 +28,7 @@ namespace hsvd {
 
 namespace {
 
-constexpr int KCHUNK = 1024;
+constexpr int KCHUNK = 2048;
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -263,7 +263,7 @@ struct Builder {
       if (g.M.cap <= 0 || g.N.cap <= 0) continue;
       const int ktot = g.K.cap + (is_tn ? 0 : g.K2.cap);
       // long K with few output tiles: split finer so the launch fills the GPU
-      const int chunk = (ktot > KCHUNK && g.mtiles * g.ntiles <= 2) ? KCHUNK / 4 : KCHUNK;
+      const int chunk = (ktot > KCHUNK && g.mtiles * g.ntiles <= 2) ? KCHUNK / 4 : KCHUNK;  // 512 or 2048
       if (ktot > chunk) {
         g.kchunk = chunk;
         g.nkc = cdiv(ktot, chunk);
@@ -905,7 +905,10 @@ struct Builder {
       for (auto& w : bw) v.push_back(which == 0 ? w.oY : (which == 1 ? w.oW : w.oR));
       return v;
     };
-    emit_orth("block.orthY", orth_list(0), 2, kp);
+    // Before a power step the sketch only needs to be well conditioned (the
+    // step re-orthonormalises), so one CholeskyQR pass; the basis that is
+    // projected on at the end gets two.
+    emit_orth("block.orthY", orth_list(0), P.q > 0 ? 1 : 2, kp);
     for (int it = 0; it < P.q; ++it) {
       std::vector<InputOp> ops;
       for (auto& w : bw)
