@@ -241,6 +241,12 @@ void hsvd_destroy(hsvd_plan_t plan);
 /* hsvd_error_string -- static description of a status code. */
 const char* hsvd_error_string(hsvd_status s);
 
+/* hsvd_last_error -- detail of the last HSVD_ECUDA returned by hsvd_run or
+ * hsvd_run_host on this plan: the failing step's name and the CUDA runtime's
+ * error string; "" when the last run launched every step.  The string is owned
+ * by the plan and valid until its next run or hsvd_destroy.  NULL plan: "". */
+const char* hsvd_last_error(hsvd_plan_t plan);
+
 /* hsvd_tree_levels -- host-only: number of MAT levels of a tree over
  * `count` leaves (ceil(log2 count); Alg. 1 DoMergeOfSlices with the odd
  * element carried), or -1 for count < 1. */

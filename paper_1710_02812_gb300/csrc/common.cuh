@@ -224,6 +224,14 @@ cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* 
 // Host-side helpers exported for checks without a GPU.
 int jacobi_pair_host(int n, int r, int s, int* p, int* q);
 bool jacobi_uses_smem(int nrcap, int nccap, bool want_v, size_t elem);
+// The one-CTA shared-memory core kernel can hold a core of this size.
+bool jacobi_sm_fits(int nrcap, int nccap, bool want_v, size_t elem);
+// Cores spread over a thread-block cluster (FP32): cluster size for a launch
+// (1 = no cluster) and the launch itself (*done false: not launched).
+int jacobi_cluster_size(int ntasks, int nrcap, int nccap, bool need_split);
+size_t jacobi_cluster_smem(int nrcap, int nccap, bool want_v, int C);
+cudaError_t launch_jacobi_cluster(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                                  int C, TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem);
 bool chol_uses_smem(int kcap, size_t elem);
 

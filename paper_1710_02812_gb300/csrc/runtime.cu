@@ -60,6 +60,7 @@ struct ProblemOut {
 
 struct PlanImpl {
   int batch = 0;
+  std::string last_error;  // step and CUDA error of the last failed run ("" if none)
   std::vector<int64_t> m, n;
   int64_t br = 0, bc = 0;
   hsvd_trunc mode = HSVD_TRUNC_FIXED_K;
@@ -1168,6 +1169,8 @@ const char* hsvd_error_string(hsvd_status s) {
   return "unknown status";
 }
 
+const char* hsvd_last_error(hsvd_plan_t plan) { return plan ? plan->impl.last_error.c_str() : ""; }
+
 int32_t hsvd_tree_levels(int64_t count) {
   if (count < 1) return -1;
   int32_t lv = 0;
@@ -1330,9 +1333,12 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
     }
     cudaEventRecord(ev[0], s);
   }
+  P.last_error.clear();
   for (size_t i = 0; i < P.steps.size(); ++i) {
-    if (P.steps[i].run(s) != cudaSuccess) {
+    const cudaError_t err = P.steps[i].run(s);
+    if (err != cudaSuccess) {
       cudaGetLastError();
+      P.last_error = P.steps[i].name + ": " + cudaGetErrorString(err);
       if (timed) P.pool.push_back(std::move(ev));
       return HSVD_ECUDA;
     }
@@ -1394,9 +1400,11 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
   std::vector<int64_t> dld(P.batch);
   for (int b = 0; b < P.batch; ++b) {
     const size_t w = (size_t)P.n[b] * P.in_elem;
-    if (cudaMemcpy2DAsync(P.staging[b], w, A[b], (size_t)lda[b] * P.in_elem, w, (size_t)P.m[b],
-                          cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    const cudaError_t e = cudaMemcpy2DAsync(P.staging[b], w, A[b], (size_t)lda[b] * P.in_elem, w,
+                                            (size_t)P.m[b], cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
       cudaGetLastError();
+      P.last_error = std::string("host-to-device copy: ") + cudaGetErrorString(e);
       return HSVD_ECUDA;
     }
     dptr[b] = P.staging[b];

@@ -18,26 +18,12 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "jacobi.cuh"
 
 namespace hsvd {
 
 namespace {
 
-template <class T>
-struct Eps;
-template <>
-struct Eps<float> {
-  static constexpr double v = 5.9604644775390625e-08;
-};
-template <>
-struct Eps<double> {
-  static constexpr double v = 1.1102230246251565e-16;
-};
-
-template <class T>
-__device__ __forceinline__ T dsqrt(T x) {
-  return sqrt(x);
-}
 
 // ------------------------------------------------------------------ Cholesky
 // In-place elimination on the unit-diagonal scaled Gram matrix Gh = S G S:
@@ -452,49 +438,6 @@ __global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict_
 }
 
 // ------------------------------------------------------------------ Jacobi
-// Round-robin (circle) ordering for n even: slot 0 pairs (r, n-1); slot s>0
-// pairs (r+s, r-s) mod (n-1).  Each unordered pair appears once per sweep and
-// the pairs of one round are disjoint.
-__host__ __device__ __forceinline__ void rr_pair(int n, int r, int s, int& p, int& q) {
-  const int m = n - 1;  // 0 <= r < m, 0 <= s < n/2, so one conditional wrap suffices
-  if (s == 0) {
-    p = r;
-    q = m;
-  } else {
-    p = r + s;
-    if (p >= m) p -= m;
-    q = r - s;
-    if (q < 0) q += m;
-  }
-}
-
-// Reciprocal square root refined by one Newton step (float: hardware
-// estimate + Newton gives ~1 ulp; double: library rsqrt).
-__device__ __forceinline__ float rsq(float x) {
-  const float r = rsqrtf(x);
-  return r * fmaf(-0.5f * x, r * r, 1.5f);
-}
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
-
-// Leading dimension of the column-major working copy: rows rounded up to the
-// bank period plus a quarter period, so the columns handled by the groups
-// of one warp start in different banks.
-__host__ __device__ __forceinline__ int jacobi_ld(int nr, int elem) {
-  const int period = elem == 8 ? 16 : 32;
-  return ((nr + period - 1) / period) * period + period / 4;
-}
-// The same for G lanes per pair (32 / G groups per warp, consecutive groups
-// handle consecutive columns): consecutive columns start G banks apart, so
-// the groups of one warp read disjoint bank ranges (8-byte elements take two
-// banks each; a warp's request spans two wavefronts anyway).
-__host__ __device__ __forceinline__ int jacobi_ld_g(int nr, int elem, int G) {
-  const int period = elem == 8 ? 16 : 32;
-  int ld = ((nr + period - 1) / period) * period;
-  if (G < 32) ld += (elem == 8 && G > 8) ? 8 : G;
-  return ld;
-}
 
 // Householder QR of the n x n column-major matrix A (ld lda) in shared or
 // global memory, overwritten by R^T (lower triangular); Q is not formed.
@@ -1201,6 +1144,373 @@ __global__ void __launch_bounds__(RMAX >= 16 ? 512 : 1024, 1) k_jacobi_sm(const 
   jacobi_finish<T, WANT_V>(tk, Mw, ldm, Vw, ldv, nr, nc, k1, k2, tp, st, sig_s, perm, &rank_s);
 }
 
+// householder_r_transpose for FP32 with groups of 8 lanes (blockDim a multiple
+// of 32): every group updates trailing columns (3-level reductions instead of
+// 5, many columns at once), and group 0, which always holds column j + 1,
+// builds reflection j + 1 right after updating that column, so a step costs
+// one CTA barrier.  vb holds two reflection buffers of n + 1 floats.
+__device__ void householder_r_transpose8(float* A, int lda, int n, float* vb) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int g = tid >> 3, lane = tid & 7, ngroups = nt >> 3;
+  const unsigned gm = 0xffu << ((tid & 31) & ~7);
+  // reflection from column j (rows >= j) into v: v[j] = 1, v[n] = tau
+  auto reflect = [&](int j, float* v) {
+    float* x = A + j * lda;
+    const float x0 = x[j];
+    float s = 0.f;
+    for (int i = j + 1 + lane; i < n; i += 8) s = fmaf(x[i], x[i], s);
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(gm, s, off);
+    const float alpha = sqrtf(s + x0 * x0);
+    float tau = 0.f, beta = x0, scale = 0.f;
+    if (s > 0.f) {
+      beta = x0 >= 0.f ? -alpha : alpha;
+      tau = (beta - x0) / beta;
+      scale = 1.f / (x0 - beta);
+    }
+    for (int i = j + 1 + lane; i < n; i += 8) v[i] = x[i] * scale;
+    if (lane == 0) {
+      v[j] = 1.f;
+      v[n] = tau;
+      x[j] = beta;
+    }
+  };
+  if (n < 2) return;
+  if (g == 0) reflect(0, vb);
+  __syncthreads();
+  for (int j = 0; j < n - 1; ++j) {
+    const float* v = vb + (j & 1) * (n + 1);
+    float* vn = vb + ((j + 1) & 1) * (n + 1);
+    const float tau = v[n];
+    for (int c = j + 1 + g; c < n; c += ngroups) {
+      float* y = A + c * lda;
+      if (tau != 0.f) {
+        float w = 0.f;
+        for (int i = j + lane; i < n; i += 8) w = fmaf(v[i], y[i], w);
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) w += __shfl_xor_sync(gm, w, off);
+        w *= tau;
+        for (int i = j + lane; i < n; i += 8) y[i] = fmaf(-w, v[i], y[i]);
+      }
+      if (c == j + 1 && c < n - 1) {
+        __syncwarp(gm);
+        reflect(c, vn);
+      }
+    }
+    __syncthreads();
+  }
+  // R is the upper triangle; write R^T in place (lower triangle) and zero the rest.
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e % n, c = e / n;
+    if (i < c) {
+      const float r = A[c * lda + i];
+      A[i * lda + c] = r;
+      A[c * lda + i] = 0.f;
+    }
+  }
+  __syncthreads();
+}
+
+// Packed pairs of FP32 values (one 64-bit register pair): Blackwell issues
+// one f32x2 FMA / multiply / add for two lanes' worth of work.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// One rotation of the column pair held by one group of 8 lanes (lane l holds
+// rows 4l..4l+3 of every chunk of 32 rows in x[] and y[]): inner products,
+// reduction over the group, rotation angle as in k_jacobi_sm, update in
+// registers.  Returns true (and cs, sn) when the pair was rotated.
+template <int RMAX, bool F2>
+__device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], float tol2, float big2, int& big,
+                                          float& cs, float& sn) {
+  float a, b, c;
+  if constexpr (F2) {
+    uint64_t a2[2] = {0, 0}, b2[2] = {0, 0}, c2[2] = {0, 0};
+#pragma unroll
+    for (int t = 0; t < RMAX / 2; ++t) {
+      const uint64_t x2 = f2_pack(xr[2 * t], xr[2 * t + 1]), y2 = f2_pack(yr[2 * t], yr[2 * t + 1]);
+      a2[t & 1] = f2_fma(x2, x2, a2[t & 1]);
+      b2[t & 1] = f2_fma(y2, y2, b2[t & 1]);
+      c2[t & 1] = f2_fma(x2, y2, c2[t & 1]);
+    }
+    float lo, hi;
+    f2_unpack(f2_add(a2[0], a2[1]), lo, hi);
+    a = lo + hi;
+    f2_unpack(f2_add(b2[0], b2[1]), lo, hi);
+    b = lo + hi;
+    f2_unpack(f2_add(c2[0], c2[1]), lo, hi);
+    c = lo + hi;
+  } else {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, c0 = 0.f, c1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < RMAX; ++t) {
+      if (t & 1) {
+        a1 = fmaf(xr[t], xr[t], a1);
+        b1 = fmaf(yr[t], yr[t], b1);
+        c1 = fmaf(xr[t], yr[t], c1);
+      } else {
+        a0 = fmaf(xr[t], xr[t], a0);
+        b0 = fmaf(yr[t], yr[t], b0);
+        c0 = fmaf(xr[t], yr[t], c0);
+      }
+    }
+    a = a0 + a1;
+    b = b0 + b1;
+    c = c0 + c1;
+  }
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) {  // the 8 lanes of the group (aligned)
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  const float ab = a * b, cc = c * c;
+  if (!(ab > 0.f && cc > tol2 * ab)) return false;
+  big |= cc > big2 * ab;
+  const float zeta = (b - a) * fast_rcp(2.f * c);
+  const float az = fabsf(zeta);
+  float t;
+  if (az < 1e18f) {
+    const float q1 = 1.f + az * az;
+    t = fast_rcp(az + q1 * rsq(q1));
+  } else {
+    t = 0.5f * fast_rcp(az);
+  }
+  if (zeta < 0.f) t = -t;
+  cs = rsq(1.f + t * t);
+  sn = cs * t;
+  if constexpr (F2) {
+    const uint64_t cs2 = f2_pack(cs, cs), sn2 = f2_pack(sn, sn), nsn2 = f2_pack(-sn, -sn);
+#pragma unroll
+    for (int u = 0; u < RMAX / 2; ++u) {
+      const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]), y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
+      f2_unpack(f2_fma(cs2, x2, f2_mul(nsn2, y2)), xr[2 * u], xr[2 * u + 1]);
+      f2_unpack(f2_fma(sn2, x2, f2_mul(cs2, y2)), yr[2 * u], yr[2 * u + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < RMAX; ++u) {
+      const float xv = xr[u], yv = yr[u];
+      xr[u] = cs * xv - sn * yv;
+      yr[u] = sn * xv + cs * yv;
+    }
+  }
+  return true;
+}
+
+template <int RMAX>
+__device__ __forceinline__ void bp_load(const float* Mw, int col, int ldm, int lane, float (&r)[RMAX]) {
+  const float4* p4 = reinterpret_cast<const float4*>(Mw + col * ldm) + lane;
+#pragma unroll
+  for (int t = 0; t < RMAX / 4; ++t) {
+    const float4 v = p4[t * 8];
+    r[4 * t] = v.x;
+    r[4 * t + 1] = v.y;
+    r[4 * t + 2] = v.z;
+    r[4 * t + 3] = v.w;
+  }
+}
+template <int RMAX>
+__device__ __forceinline__ void bp_store(float* Mw, int col, int ldm, int lane, const float (&r)[RMAX]) {
+  float4* p4 = reinterpret_cast<float4*>(Mw + col * ldm) + lane;
+#pragma unroll
+  for (int t = 0; t < RMAX / 4; ++t) p4[t * 8] = make_float4(r[4 * t], r[4 * t + 1], r[4 * t + 2], r[4 * t + 3]);
+}
+__device__ __forceinline__ void bp_rotate_v(float* Vw, int ldv, int p, int q, int nc, int lane, float cs, float sn) {
+  float* vx = Vw + p * ldv;
+  float* vy = Vw + q * ldv;
+  for (int i = lane; i < nc; i += 8) {
+    const float xv = vx[i], yv = vy[i];
+    vx[i] = cs * xv - sn * yv;
+    vy[i] = sn * xv + cs * yv;
+  }
+}
+
+// FP32 core SVD with a block-pair ordering (8 lanes per column pair, columns
+// in blocks of 4).  A sweep is: the pairs inside each block (3 rounds, two
+// blocks per warp, through shared memory), then nb - 1 block rounds of the
+// round-robin ordering over the nb blocks; in a block round warp w takes the
+// block pair (I, J), its four lane groups hold columns I_g and J_g in
+// registers, and four inner rounds pair I_g with J_{(g+t) mod 4}, passing the
+// J columns from group to group by warp shuffles.  Every column pair is
+// rotated once per sweep, as in the cyclic ordering; shared memory is read and
+// written once per block round instead of once per round, and the CTA
+// barrier is taken once per block round.
+template <bool WANT_V, int RMAX, bool F2>
+__global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* __restrict__ tasks, int nccap,
+                                                      TruncParams tp, DevStatus* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* __restrict__ Mw = reinterpret_cast<float*>(smem_raw);
+  __shared__ float sig_s[512];
+  __shared__ int perm[512];
+  __shared__ int rank_s;
+  __shared__ float hh_scratch[520];
+  constexpr int G = 8;
+  constexpr int rows_pad = G * RMAX;
+  const JacobiTask<float>& tk = tasks[blockIdx.x];
+  int nr, nc, k1 = 0, k2 = 0;
+  if (tk.load == 1) {
+    k1 = eff(tk.k1);
+    k2 = eff(tk.k2);
+    nr = nc = k1 + k2;
+  } else {
+    nr = eff(tk.nr);
+    nc = eff(tk.nc);
+  }
+  const int n8 = (nc + 7) & ~7;             // columns in blocks of 4, an even number of blocks
+  const int ncc8 = (nccap + 7) & ~7;
+  const int ldm = jacobi_ld_g(rows_pad, 4, G);
+  const int ldv = jacobi_ld(ncc8, 4);
+  float* __restrict__ Vw = WANT_V ? (Mw + ldm * ncc8) : nullptr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int e = tid; e < rows_pad * n8; e += nt) {
+    const int i = e % rows_pad, j = e / rows_pad;
+    float v = 0.f;
+    if (j < nc && i < nr) {
+      if (tk.load == 0) {
+        v = tk.src[(int64_t)i * tk.rs + (int64_t)j * tk.cs];
+      } else {
+        const int ei = j, ej = i;  // element (i, j) of E^T is E[j][i]
+        if (ei < k1) {
+          if (ej < k1)
+            v = (ei == ej) ? tk.s1[ei] : 0.f;
+          else {
+            float p = tk.P[(int64_t)ei * tk.ldp + (ej - k1)];
+            if (tk.P2) p += tk.P2[(int64_t)ei * tk.ldp + (ej - k1)];
+            v = p * tk.s2[ej - k1];
+          }
+        } else if (ej >= k1) {
+          v = tk.R[(int64_t)(ei - k1) * tk.ldr + (ej - k1)] * tk.s2[ej - k1];
+        }
+      }
+    }
+    Mw[j * ldm + i] = v;
+  }
+  if (WANT_V)
+    for (int e = tid; e < n8 * n8; e += nt) {
+      const int i = e % n8, j = e / n8;
+      Vw[j * ldv + i] = (i == j) ? 1.f : 0.f;
+    }
+  if (tk.load == 1 && nr > 1) {
+    __syncthreads();
+    householder_r_transpose8(Mw, ldm, nr, hh_scratch);
+  }
+  __syncthreads();
+
+  const int nb = n8 / 4;
+  const int warp = tid >> 5, grp = (tid & 31) >> 3, lane = tid & 7;
+  const double told = 4.0 * Eps<float>::v * sqrt((double)(nr > 1 ? nr : 1));
+  const float tol2 = static_cast<float>(told * told);
+  const float big2 = static_cast<float>(told);
+  bool converged = (nc <= 1);
+  int sweep = 0;
+  for (; sweep < tp.max_sweeps && !converged; ++sweep) {
+    int big = 0;
+    // pairs inside each block: warp w holds blocks 2w (groups 0, 1) and 2w + 1
+    {
+      const int blk = 2 * warp + (grp >> 1), h = grp & 1;
+      const bool act = blk < nb;
+#pragma unroll 1
+      for (int t = 0; t < 3; ++t) {
+        // t = 0: (0,1)(2,3); t = 1: (0,2)(1,3); t = 2: (0,3)(1,2)
+        const int pa = h == 0 ? 0 : (t == 0 ? 2 : 1);
+        const int pb = h == 0 ? t + 1 : (t == 2 ? 2 : 3);
+        const int p = 4 * blk + pa, q = 4 * blk + pb;
+        float xr[RMAX], yr[RMAX];
+        if (act) {
+          bp_load<RMAX>(Mw, p, ldm, lane, xr);
+          bp_load<RMAX>(Mw, q, ldm, lane, yr);
+        } else {
+#pragma unroll
+          for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
+        }
+        float cs = 1.f, sn = 0.f;
+        const bool rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+        if (act && rot) {
+          bp_store<RMAX>(Mw, p, ldm, lane, xr);
+          bp_store<RMAX>(Mw, q, ldm, lane, yr);
+          if (WANT_V) bp_rotate_v(Vw, ldv, p, q, nc, lane, cs, sn);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // block rounds: warp w takes block pair w of the round
+    const bool wact = warp < nb / 2;  // warps past this core's block pairs idle
+    for (int R = 0; R < nb - 1; ++R) {
+      int I = 0, J = 0;
+      float xr[RMAX], yr[RMAX];
+      if (wact) {
+        rr_pair(nb, R, warp, I, J);
+        bp_load<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
+        bp_load<RMAX>(Mw, 4 * J + grp, ldm, lane, yr);
+      } else {
+#pragma unroll
+        for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
+      }
+#pragma unroll 1
+      for (int t = 0; t < 4; ++t) {
+        float cs = 1.f, sn = 0.f;
+        const bool rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+        if (WANT_V) {
+          if (wact && rot) bp_rotate_v(Vw, ldv, 4 * I + grp, 4 * J + ((grp + t) & 3), nc, lane, cs, sn);
+          __syncwarp();
+        }
+        if (t < 3) {
+#pragma unroll
+          for (int u = 0; u < RMAX; ++u) yr[u] = __shfl_sync(0xffffffffu, yr[u], (tid + 8) & 31);
+        }
+      }
+      if (wact) {
+        bp_store<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
+        bp_store<RMAX>(Mw, 4 * J + ((grp + 3) & 3), ldm, lane, yr);
+      }
+      __syncthreads();
+    }
+    converged = !__syncthreads_or(big);
+  }
+  if (!converged && tid == 0 && st) atomicAdd(&st->not_converged, 1);
+  if (tid == 0 && st) {
+    atomicAdd(&st->sweeps, sweep);
+    atomicAdd(&st->cores, 1);
+  }
+
+  const int ngroups = nt / G, gid = tid / G;
+  const unsigned gm = 0xffu << ((tid & 31) & ~7);
+  for (int j = gid; j < nc; j += ngroups) {
+    const float* x = Mw + j * ldm;
+    float a = 0.f;
+    for (int i = lane; i < nr; i += G) a += x[i] * x[i];
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) a += __shfl_xor_sync(gm, a, off);
+    if (lane == 0) sig_s[j] = isfinite(a) ? sqrtf(a) : -1.f;
+  }
+  __syncthreads();
+  jacobi_finish<float, WANT_V>(tk, Mw, ldm, Vw, ldv, nr, nc, k1, k2, tp, st, sig_s, perm, &rank_s);
+}
+
 // Lanes per pair G and rows per lane RMAX for a launch: all pairs of a round
 // at once when they fit 512 threads, else groups loop over pairs.
 static void jacobi_shape(int nrcap, int nccap, int& G, int& rmax) {
@@ -1261,6 +1571,16 @@ static bool jacobi_sm_shape(int nrcap, int& G, int& rmax) {
   return G <= 32;
 }
 
+bool jacobi_sm_fits(int nrcap, int nccap, bool want_v, size_t elem) {
+  int G, rmax;
+  if (!jacobi_sm_shape(nrcap, G, rmax)) return false;
+  const int ncc = nccap + (nccap & 1);
+  const size_t bytes =
+      ((size_t)jacobi_ld_g(G * rmax, (int)elem, G) * ncc + (want_v ? (size_t)jacobi_ld(ncc, (int)elem) * ncc : 0)) *
+      elem;
+  return bytes <= 200 * 1024;
+}
+
 template <class T, bool V>
 static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, TruncParams tp,
                                    DevStatus* st, cudaStream_t s, bool* done) {
@@ -1300,13 +1620,83 @@ static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int 
   }
 }
 
+// Block-pair kernel (FP32, up to 128 columns and 128 rows): 8 lanes per pair,
+// ncc8 / 8 warps.  HSVD_JACOBI_BP=0 turns it off (for comparisons).
+static bool jacobi_bp_enabled() {
+  static bool on = [] {
+    const char* e = std::getenv("HSVD_JACOBI_BP");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+static size_t jacobi_bp_bytes(int rmax, int nccap, bool want_v) {
+  const int ncc8 = (nccap + 7) & ~7;
+  return ((size_t)jacobi_ld_g(8 * rmax, 4, 8) * ncc8 + (want_v ? (size_t)jacobi_ld(ncc8, 4) * ncc8 : 0)) *
+         sizeof(float);
+}
+static cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                                    TruncParams tp, DevStatus* st, cudaStream_t s, bool* done) {
+  *done = false;
+  if (!jacobi_bp_enabled() || nccap < 8 || nccap > 128 || nrcap > 128) return cudaSuccess;
+  const int rows = nrcap <= 32 ? 32 : nrcap <= 64 ? 64 : 128;
+  const int rmax = rows / 8;
+  const size_t bytes = jacobi_bp_bytes(rmax, nccap, want_v);
+  if (bytes > 200 * 1024) return cudaSuccess;
+  const int threads = ((nccap + 7) & ~7) * 4;  // one warp per block pair
+  auto go = [&](auto kern) -> cudaError_t {
+    if (bytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<ntasks, threads, bytes, s>>>(tasks, nccap, tp, st);
+    *done = true;
+    return cudaGetLastError();
+  };
+  // Packed f32x2 arithmetic for the rotations (HSVD_JACOBI_F2=0: scalar).
+  static const bool f2 = [] {
+    const char* e = std::getenv("HSVD_JACOBI_F2");
+    return !(e && e[0] == '0');
+  }();
+  if (f2) {
+    switch (rmax * 2 + (want_v ? 1 : 0)) {
+      case 8: return go(k_jacobi_bp<false, 4, true>);
+      case 9: return go(k_jacobi_bp<true, 4, true>);
+      case 16: return go(k_jacobi_bp<false, 8, true>);
+      case 17: return go(k_jacobi_bp<true, 8, true>);
+      case 32: return go(k_jacobi_bp<false, 16, true>);
+      case 33: return go(k_jacobi_bp<true, 16, true>);
+      default: return cudaSuccess;
+    }
+  }
+  switch (rmax * 2 + (want_v ? 1 : 0)) {
+    case 8: return go(k_jacobi_bp<false, 4, false>);
+    case 9: return go(k_jacobi_bp<true, 4, false>);
+    case 16: return go(k_jacobi_bp<false, 8, false>);
+    case 17: return go(k_jacobi_bp<true, 8, false>);
+    case 32: return go(k_jacobi_bp<false, 16, false>);
+    case 33: return go(k_jacobi_bp<true, 16, false>);
+    default: return cudaSuccess;
+  }
+}
+
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                           TruncParams tp, DevStatus* st, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   if (nccap > 512 || nrcap > 512) return cudaErrorInvalidValue;
   bool done = false;
-  cudaError_t e = want_v ? launch_jacobi_sm<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s, &done)
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
+    if (e != cudaSuccess || done) return e;
+    // Cores one CTA cannot hold are spread over a cluster.
+    const int C = jacobi_cluster_size(ntasks, nrcap, nccap, !jacobi_sm_fits(nrcap, nccap, want_v, sizeof(T)));
+    if (C >= 2) {
+      e = launch_jacobi_cluster(tasks, ntasks, nrcap, nccap, want_v, C, tp, st, s, &done);
+      if (e != cudaSuccess || done) return e;
+    }
+  }
+  e = want_v ? launch_jacobi_sm<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s, &done)
                          : launch_jacobi_sm<T, false>(tasks, ntasks, nrcap, nccap, tp, st, s, &done);
   if (e != cudaSuccess || done) return e;
   return want_v ? launch_jacobi_v<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s)

@@ -26,7 +26,7 @@ WHERE = {"host": 0, "device": 1}
 EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd_factors",
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
-            "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc")
+            "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -101,6 +101,8 @@ def lib():
         L.hsvd_step_times.restype = ctypes.c_int
         L.hsvd_block_svd_noalloc.argtypes = [P, i64, i32, i32, i32, i32, P, i64, P, P, P]
         L.hsvd_block_svd_noalloc.restype = ctypes.c_int
+        L.hsvd_last_error.argtypes = [P]
+        L.hsvd_last_error.restype = ctypes.c_char_p
         _lib_handle = L
     return _lib_handle
 
@@ -148,13 +150,26 @@ def hsvd_plan(m: Sequence[int], n: Sequence[int], block_rows: int, block_cols: i
 def hsvd_run(plan, ptrs: Sequence[int], lda: Sequence[int], stream=None):
     arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
     ld = (ctypes.c_int64 * len(lda))(*[int(v) for v in lda])
-    _check(lib().hsvd_run(plan, arr, ld, _stream_ptr(stream)), "hsvd_run")
+    code = lib().hsvd_run(plan, arr, ld, _stream_ptr(stream))
+    if code != HSVD_OK:
+        raise HsvdError(code, "hsvd_run" + _detail(plan))
 
 
 def hsvd_run_host(plan, ptrs: Sequence[int], lda: Sequence[int], stream=None):
     arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
     ld = (ctypes.c_int64 * len(lda))(*[int(v) for v in lda])
-    _check(lib().hsvd_run_host(plan, arr, ld, _stream_ptr(stream)), "hsvd_run_host")
+    code = lib().hsvd_run_host(plan, arr, ld, _stream_ptr(stream))
+    if code != HSVD_OK:
+        raise HsvdError(code, "hsvd_run_host" + _detail(plan))
+
+
+def hsvd_last_error(plan) -> str:
+    return (lib().hsvd_last_error(plan) or b"").decode()
+
+
+def _detail(plan) -> str:
+    d = hsvd_last_error(plan)
+    return f" [{d}]" if d else ""
 
 
 def hsvd_status_query(plan, sync: bool = True) -> dict:

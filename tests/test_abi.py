@@ -110,6 +110,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.hsvd_factors(None, 0, None, None, 0, None, None, 0, 0, None) == hsvd.HSVD_EINVAL
     assert lib.hsvd_workspace_bytes(None) == 0
     assert lib.hsvd_launches_per_run(None) == -1
+    assert lib.hsvd_last_error(None) == b""
     lib.hsvd_destroy(None)
 
 

@@ -303,3 +303,23 @@ def test_bf16_mixed_row_then_col_tensor_core():
     (got,), st, _ = run_gpu([xb], 128, 256, "fixed_k", 20, "bf16_mixed", tree="row_then_col", oversample=48)
     ref = oracle_run(xb, 128, 256, "fixed_k", 20, "bf16_mixed", tree="row_then_col")
     check(xb, got, ref, "bf16_mixed", "tc row_then_col", s_true=np.exp(-np.arange(200) / 20.0))
+
+
+# ---------------------------------------------------------------- cores on thread-block clusters
+
+@pytest.mark.parametrize("m,n,br,bc,k", [
+    (2048, 2048, 1024, 1024, 128),  # 256 x 256 block and merge cores, 8-CTA clusters
+    (2048, 2048, 256, 256, 100),    # 200-row cores: 64 block cores on 2-CTA clusters, merges on 4
+])
+def test_fp32_wide_cores_on_clusters(m, n, br, bc, k):
+    """Cores too large for one CTA (k = 128 gives 256 x 256 block sketch and
+    merge cores) and levels with few cores run spread over a cluster.  The
+    spectrum exp(-i/40) keeps absolute gaps near sigma_k well above FP32
+    rounding of the input (a 1/i spectrum does not: an input perturbation of
+    FP32 size alone turns its 99th vector by ~1e-3 rad)."""
+    s_true = np.exp(-np.arange(160) / 40.0)
+    x = W.planted(m, n, s_true, noise=1e-6, tag=81 + br).astype(np.float32)
+    (got,), st, _ = run_gpu([x], br, bc, "fixed_k", k, "f32", power_iters=2)
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0
+    ref = oracle_run(x, br, bc, "fixed_k", k, "f32")
+    check(x, got, ref, "f32", f"clusters {m}x{n}/{br}", s_true=s_true)
