@@ -42,10 +42,20 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 
 
 def workload_config(prec, q):
-    return {"workload": "exp_decay_8192", "m": M, "n": N, "block": [BR, BC], "grid": [M // BR, N // BC],
-            "k": K, "spectrum": "s_i=exp(-i/20), 512 modes", "noise": NOISE, "tree": "col_then_row",
-            "path": prec, "power_iters": q, "input_dtype": "f32",
-            "l2": "input 268 MB > 129 MB L2 (no flush needed)"}
+    mb = M * N * 4 / 1e6
+    l2 = (f"input {mb:.0f} MB > 129 MB L2 (no flush needed)" if mb > 129 else
+          f"input {mb:.0f} MB fits L2: profiling size only, not a bench line")
+    return {"workload": f"exp_decay_{M}" if M == N else f"exp_decay_{M}x{N}", "m": M, "n": N, "block": [BR, BC],
+            "grid": [M // BR, N // BC], "k": K, "spectrum": f"s_i=exp(-i/20), {MODES} modes", "noise": NOISE,
+            "tree": "col_then_row", "path": prec, "power_iters": q, "input_dtype": "f32", "l2": l2}
+
+
+def set_size(size):
+    """--size S: the same construction on an S x S matrix (same blocks, k and
+    spectrum) -- small cases for profiler captures."""
+    global M, N, MODES
+    M = N = size
+    MODES = min(512, size)
 
 
 def make_input():
@@ -355,8 +365,14 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparison run")
     ap.add_argument("--power-iters", dest="power_iters", type=int, default=1)
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="matrix size (default 8192, the bench workload; smaller sizes are for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.size != 8192:
+        if args.size < BR or args.size % BR:
+            ap.error(f"--size must be a multiple of the {BR}-row block")
+        set_size(args.size)
     world, rank, local = dist_init()
     try:
         if args.impl == "reference":
