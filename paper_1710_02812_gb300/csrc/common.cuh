@@ -197,11 +197,23 @@ struct TcTask {
   int M, N, K;
   float* D;
   int64_t ldd;
+  int kchunk_tiles;    // split-K: 64-wide K tiles per chunk (0: one chunk)
+  int ldp;             // row stride of a partial tile (elements)
+  float* part;         // split-K partials [chunk][M][ldp], or nullptr (write D)
 };
 struct TcItem {
-  int task, mt;  // task and 128-row tile
+  int task, mt, kc;  // task, 128-row tile, K chunk
+};
+// Sum of the split-K partials of one tensor-core task into its D (chunks in
+// order, FP32 round to nearest).
+struct TcRedTask {
+  const float* part;
+  int nkc, M, N, ldp;
+  float* D;
+  int64_t ldd;
 };
 bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+cudaError_t launch_tc_reduce(const TcRedTask* tasks, const int2* items, int nitems, cudaStream_t s);
 bool tc_available();  // the driver's tensor-map encoder could be resolved
 
 // A factor B (K x N FP32, row-major, ld ldb) written as its BF16 transpose:

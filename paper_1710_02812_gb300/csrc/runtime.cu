@@ -465,7 +465,9 @@ struct Builder {
     std::vector<int3> bti;
     std::vector<TcTask> tc;
     std::vector<TcItem> tci;
-    double flops = 0, bytes = 0;
+    std::vector<TcRedTask> red;
+    std::vector<int2> rdi;
+    double flops = 0, bytes = 0, rbytes = 0;
     for (size_t t = 0; t < ops.size(); ++t) {
       const InputOp& o = ops[t];
       const int M = o.xt ? o.w : o.h, K = o.xt ? o.h : o.w;
@@ -495,8 +497,38 @@ struct Builder {
       k.K = K;
       k.D = reinterpret_cast<float*>(o.C);
       k.ldd = o.ldc;
+      // Long K is split into chunks of at most 16 K tiles (1024), at most 16
+      // chunks, summed afterwards in FP32: the tensor cores' FP32
+      // accumulation drifts toward zero with the number of accumulation steps
+      // (relative ~1.5e-5 over K = 8192 in one accumulator), and the chunks
+      // also give short, wide products more CTAs.
+      const int ktiles = (K + 63) / 64;
+      int nkc = 1;
+      if (ktiles > 32) {
+        nkc = std::min(16, (ktiles + 15) / 16);
+        k.kchunk_tiles = (ktiles + nkc - 1) / nkc;
+        nkc = (ktiles + k.kchunk_tiles - 1) / k.kchunk_tiles;
+        k.ldp = ((o.N.cap + 3) / 4) * 4;
+        k.part = alloc<float>((size_t)nkc * M * k.ldp);
+        TcRedTask rt;
+        rt.part = k.part;
+        rt.nkc = nkc;
+        rt.M = M;
+        rt.N = o.N.cap;
+        rt.ldp = k.ldp;
+        rt.D = k.D;
+        rt.ldd = k.ldd;
+        for (int r = 0; r < (M + 15) / 16; ++r) rdi.push_back(make_int2((int)red.size(), r));
+        red.push_back(rt);
+        rbytes += (double)(nkc + 1) * M * o.N.cap * 4;
+      } else {
+        k.kchunk_tiles = 0;
+        k.ldp = 0;
+        k.part = nullptr;
+      }
       tc.push_back(k);
-      for (int mt = 0; mt < (M + 127) / 128; ++mt) tci.push_back(TcItem{(int)t, mt});
+      for (int mt = 0; mt < (M + 127) / 128; ++mt)
+        for (int kc = 0; kc < nkc; ++kc) tci.push_back(TcItem{(int)t, mt, kc});
       flops += 2.0 * M * o.N.cap * K;
       bytes += (double)M * K * 2 + (double)o.N.cap * K * 2 * per + (double)M * o.N.cap * 4;
     }
@@ -512,6 +544,14 @@ struct Builder {
                                                    &p->d_status->tc_timeouts, s);
                            }});
     tag(8, (int)ops.size(), bmax, flops, bytes);
+    if (!red.empty()) {
+      const size_t b5 = P.add_blob(red), b6 = P.add_blob(rdi);
+      const int n6 = (int)rdi.size();
+      P.steps.push_back(Step{name + ".reduce", [p, b5, b6, n6](cudaStream_t s) {
+                               return launch_tc_reduce(p->table<TcRedTask>(b5), p->table<int2>(b6), n6, s);
+                             }});
+      tag(3, (int)red.size(), 0, 0, rbytes);
+    }
   }
 
   // -------------------------------------------------------------- small steps

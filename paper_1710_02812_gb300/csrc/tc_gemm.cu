@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
   const TcTask tk = tasks[it.task];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool has_lo = tk.b2_row0 >= 0;
-  const int nk = (tk.K + TC_BK - 1) / TC_BK;
+  const int nk_all = (tk.K + TC_BK - 1) / TC_BK;
+  const int kt0 = tk.kchunk_tiles > 0 ? it.kc * tk.kchunk_tiles : 0;
+  const int nk = tk.kchunk_tiles > 0 ? min(nk_all - kt0, tk.kchunk_tiles) : nk_all;  // >= 1 by construction
   const uint32_t a_bytes = TC_BM * TC_BK * 2;
   const uint32_t b_bytes = static_cast<uint32_t>(bmax) * TC_BK * 2;
   const uint32_t stage_bytes = a_bytes + 2u * b_bytes;
@@ -196,9 +198,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
       if (*(volatile int*)&failed) break;
       unsigned char* st = base + s * stage_bytes;
       mbar_arrive_expect_tx(&full_bar[s], a_bytes + (has_lo ? 2u : 1u) * b_bytes);
-      tma_load_2d(st, amap, &full_bar[s], tk.a_col0 + kt * TC_BK, arow);
-      tma_load_2d(st + a_bytes, bmap, &full_bar[s], kt * TC_BK, tk.b_row0);
-      if (has_lo) tma_load_2d(st + a_bytes + b_bytes, bmap, &full_bar[s], kt * TC_BK, tk.b2_row0);
+      const int kx = (kt0 + kt) * TC_BK;
+      tma_load_2d(st, amap, &full_bar[s], tk.a_col0 + kx, arow);
+      tma_load_2d(st + a_bytes, bmap, &full_bar[s], kx, tk.b_row0);
+      if (has_lo) tma_load_2d(st + a_bytes + b_bytes, bmap, &full_bar[s], kx, tk.b2_row0);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -244,11 +247,14 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
     tc_fence_after();
     const int row = warp * 32 + lane;
     const int gm = it.mt * TC_BM + row;
+    // split-K chunks write their partial tile; the single chunk writes D
+    float* const dst = tk.part ? tk.part + static_cast<int64_t>(it.kc) * tk.M * tk.ldp : tk.D;
+    const int64_t ldo = tk.part ? tk.ldp : tk.ldd;
     float v[32];
     for (int c0 = 0; c0 < bmax; c0 += 32) {
       tmem_ld32(tacc + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
       if (gm < tk.M) {
-        float* drow = tk.D + static_cast<int64_t>(gm) * tk.ldd + c0;
+        float* drow = dst + static_cast<int64_t>(gm) * ldo + c0;
         if (c0 + 32 <= tk.N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
 #pragma unroll
           for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(drow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
@@ -264,6 +270,44 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
   __syncthreads();
   if (warp == 0) tmem_dealloc(tacc, ncols);
   (void)mma_done;
+}
+
+// One CTA per (task, 16-row tile): rows x columns in float4 groups when the
+// strides allow, chunks summed in order.
+__global__ void __launch_bounds__(256) k_tc_reduce(const TcRedTask* __restrict__ tasks,
+                                                   const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const TcRedTask tk = tasks[it.x];
+  const int r0 = it.y * 16;
+  const int64_t cs = static_cast<int64_t>(tk.M) * tk.ldp;
+  const bool vec = (tk.N % 4 == 0) && (tk.ldp % 4 == 0) && (tk.ldd % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(tk.D) & 15) == 0);
+  if (vec) {
+    const int nq = tk.N / 4;
+    for (int e = threadIdx.x; e < 16 * nq; e += blockDim.x) {
+      const int r = r0 + e / nq, q = e % nq;
+      if (r >= tk.M) continue;
+      const float* p = tk.part + static_cast<int64_t>(r) * tk.ldp + 4 * q;
+      float4 acc = *reinterpret_cast<const float4*>(p);
+      for (int c = 1; c < tk.nkc; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(p + c * cs);
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+      *reinterpret_cast<float4*>(tk.D + static_cast<int64_t>(r) * tk.ldd + 4 * q) = acc;
+    }
+  } else {
+    for (int e = threadIdx.x; e < 16 * tk.N; e += blockDim.x) {
+      const int r = r0 + e / tk.N, c0 = e % tk.N;
+      if (r >= tk.M) continue;
+      const float* p = tk.part + static_cast<int64_t>(r) * tk.ldp + c0;
+      float acc = p[0];
+      for (int c = 1; c < tk.nkc; ++c) acc += p[c * cs];
+      tk.D[static_cast<int64_t>(r) * tk.ldd + c0] = acc;
+    }
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -328,6 +372,12 @@ cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* 
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k_tc_gemm<<<nitems, 128, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, stages, bmax, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce(const TcRedTask* tasks, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  k_tc_reduce<<<nitems, 256, 0, s>>>(tasks, items);
   return cudaGetLastError();
 }
 

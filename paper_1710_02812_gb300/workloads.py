@@ -143,3 +143,99 @@ def power_law(m: int, n: int, modes: int = 512, noise: float = 1e-6, tag: int = 
               dtype=np.float32):
     s = (np.arange(modes) + 1.0) ** -1.5
     return planted(m, n, s, noise=noise, tag=tag, dtype=dtype)
+
+
+# ---------------------------------------------------------------- on-device recipes
+# The largest configurations (a 65536 x 65536 FP32 matrix is 17 GB; the
+# 256-matrix batch is ~22 GB) are generated directly in device memory with
+# torch's seeded generator: the same recipes as above, a different random
+# stream.  They serve the full-size GPU tests, which check properties that
+# hold at any size and, where the oracle can afford it, individual matrices
+# copied back to the host.
+
+def _torch_gen(tag: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(SEED_BASE + int(tag))
+    return g
+
+
+def orthonormal_device(m: int, r: int, g, device):
+    """Q factor (diag(R) > 0) of a seeded m x r Gaussian, FP64 on the device."""
+    import torch
+    a = torch.randn((m, r), generator=g, device=device, dtype=torch.float64)
+    q, rr = torch.linalg.qr(a)
+    d = torch.sign(torch.diagonal(rr))
+    d[d == 0] = 1
+    return q * d[None, :]
+
+
+def planted_device(m: int, n: int, s, noise: float = 0.0, tag: int = 0, device="cuda",
+                   chunk_rows: int = 4096):
+    """A = U diag(s) V^T + noise * N(0, 1) as FP32 on the device (U, V with
+    orthonormal columns; the noise-free part has singular values exactly s
+    up to FP32 storage)."""
+    import torch
+    s = torch.as_tensor(np.asarray(s, dtype=np.float64), device=device)
+    g = _torch_gen(tag, device)
+    u = orthonormal_device(m, s.numel(), g, device)
+    v = orthonormal_device(n, s.numel(), g, device)
+    us = (u * s[None, :]).to(torch.float32)
+    vt = v.t().contiguous().to(torch.float32)
+    a = torch.empty((m, n), dtype=torch.float32, device=device)
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        blk = us[r0:r1] @ vt
+        if noise:
+            blk += noise * torch.randn((r1 - r0, n), generator=g, device=device, dtype=torch.float32)
+        a[r0:r1] = blk
+    return a
+
+
+def power_law_65536(device="cuda"):
+    """65536^2 FP32, s_i = (i+1)^-1.5 over 512 modes, noise 1e-6; 64 x 64
+    grid of 1024^2 blocks, k = 128."""
+    s = (np.arange(512) + 1.0) ** -1.5
+    return planted_device(65536, 65536, s, noise=1e-6, tag=5, device=device), \
+        dict(block_rows=1024, block_cols=1024, k=128, s=s)
+
+
+def pod_fourier_device(m: int = 32768, n: int = 16384, modes: int = 40, noise: float = 1e-3,
+                       tag: int = 3, device="cuda", chunk_rows: int = 4096, stats=None):
+    """pod_fourier on the device, BF16 storage; also returns the coefficient
+    matrix C (modes x n, FP64 on the host), whose singular values are those of
+    the noise-free part (the modes are orthonormal).  stats (a dict), if
+    given, receives the Frobenius norm of the BF16 storage rounding."""
+    import torch
+    g = _torch_gen(tag, device)
+    xg = torch.arange(m, dtype=torch.float64, device=device) / m
+    phi = torch.empty((m, modes), dtype=torch.float64, device=device)
+    for j in range(modes):
+        q = j // 2 + 1
+        phi[:, j] = torch.cos(2 * np.pi * q * xg) if j % 2 == 0 else torch.sin(2 * np.pi * q * xg)
+    phi /= torch.linalg.norm(phi, dim=0, keepdim=True)
+    c = torch.randn((modes, n), generator=g, device=device, dtype=torch.float64)
+    c /= (torch.arange(1, modes + 1, dtype=torch.float64, device=device) ** 2)[:, None]
+    phif, cf = phi.to(torch.float32), c.to(torch.float32)
+    a = torch.empty((m, n), dtype=torch.bfloat16, device=device)
+    rounding2 = 0.0
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        blk = phif[r0:r1] @ cf
+        blk += noise * torch.randn((r1 - r0, n), generator=g, device=device, dtype=torch.float32)
+        a[r0:r1] = blk.to(torch.bfloat16)
+        rounding2 += float(((a[r0:r1].float() - blk).double() ** 2).sum())
+    if stats is not None:
+        stats["rounding_fro"] = rounding2 ** 0.5
+    return a, c.cpu().numpy()
+
+
+def ragged_batch_device(count: int = 256, tag: int = 4, device="cuda", noise: float = 1e-4):
+    """The many-matrix batch on the device: sizes from ragged_sizes, each
+    matrix planted with s_i = exp(-i/r) / r; returns (matrices, sizes)."""
+    sizes = ragged_sizes(count, tag=tag)
+    mats = []
+    for i, (m, n, r) in enumerate(sizes):
+        s = np.exp(-np.arange(r) / r) / r
+        mats.append(planted_device(m, n, s, noise=noise, tag=10000 + 7 * tag + i, device=device))
+    return mats, sizes
