@@ -47,6 +47,13 @@ Readings of points where the paper is silent, garbled or ambiguous:
 7. "V_r is an r x m orthogonal matrix" means n x r with orthonormal columns.
 8. Signs of singular vectors are not unique; results are normalised so the
    largest-magnitude entry of each U column is positive (V follows).
+9. Alg. 2 (iterative improvement) measures Error = ||Sigma_hat - Sigma_tilde||_2
+   / ||Sigma_hat||_2 of diagonal matrices: the spectral norm, i.e. the largest
+   |sigma_hat_i - sigma_tilde_i| over sigma_hat_1 (a value missing from one of
+   the two lists counts as zero).
+10. Alg. 2 as printed never updates V_hat inside its loop, so every pass would
+   repeat the same computation; read as V_hat <- V_tilde after each pass (the
+   power-iteration reading the paper gives for the algorithm).
 """
 from __future__ import annotations
 
@@ -303,3 +310,50 @@ def relative_error(x_k: np.ndarray, xhat_k: np.ndarray) -> float:
     """||X_k - Xhat_k||_F / ||X_k||_F, the paper's error measure (Section 4)."""
     den = np.linalg.norm(x_k)
     return float(np.linalg.norm(x_k - xhat_k) / den) if den > 0 else 0.0
+
+
+@dataclass
+class Refined:
+    u: np.ndarray
+    s: np.ndarray
+    v: np.ndarray
+    errors: List[float]
+
+    @property
+    def iterations(self) -> int:
+        return len(self.errors)
+
+
+def iterative_improvement(x, v_hat, s_hat, eps: float = 1e-3, max_iters: int = 50,
+                          rank_tol: float = 0.0) -> Refined:
+    """Alg. 2 (iterative improvement), readings 9 and 10: repeat
+    Ũ_i, Σ̃_i, Ṽ_i^T = SVD(X V̂);  Ũ, Σ̃, Ṽ^T = SVD(Ũ_i^T X);
+    Error = max_i |σ̂_i - σ̃_i| / σ̂_1;  Σ̂ = Σ̃;  V̂ = Ṽ
+    while Error > eps (at most max_iters passes); return Û = Ũ_i Ũ, Σ̂, V̂.
+    Singular values at or below rank_tol * σ_1 of a pass are dropped (with
+    their vectors), as every truncation on the path does."""
+    x = np.asarray(x, dtype=np.float64)
+    v_hat = np.asarray(v_hat, dtype=np.float64)
+    s_hat = np.asarray(s_hat, dtype=np.float64)
+    errors: List[float] = []
+    u_hat = np.zeros((x.shape[0], 0))
+
+    def keep(u, s, v):
+        r = int(np.sum(s > rank_tol * s[0])) if s.size and s[0] > 0 else 0
+        return u[:, :r], s[:r], v[:, :r]
+
+    for _ in range(max(1, max_iters)):
+        ui, si, _ = keep(*thin_svd(x @ v_hat))
+        ut, st, vt = keep(*thin_svd(ui.T @ x))
+        r = max(s_hat.size, st.size)
+        a = np.zeros(r)
+        b = np.zeros(r)
+        a[:s_hat.size] = s_hat
+        b[:st.size] = st
+        err = float(np.max(np.abs(a - b)) / s_hat[0]) if s_hat.size and s_hat[0] > 0 else 0.0
+        errors.append(err)
+        u_hat, s_hat, v_hat = ui @ ut, st, vt
+        if err <= eps:
+            break
+    u_hat, s_hat, v_hat = normalise_signs(u_hat, s_hat, v_hat)
+    return Refined(u_hat, s_hat, v_hat, errors)

@@ -324,3 +324,66 @@ def test_golden_fixtures():
             np.testing.assert_allclose(np.abs(res.u), np.array(case["u_abs"]), atol=1e-12)
         if "v_abs" in case:
             np.testing.assert_allclose(np.abs(res.v), np.array(case["v_abs"]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- Alg. 2 (iterative improvement)
+
+def test_iterative_improvement_exact_rank_stops_after_one_pass():
+    """On an exactly rank-r input the MAT result is already exact: one pass,
+    Error at rounding level, the planted sigma and subspaces unchanged."""
+    s_true = np.array([5.0, 3.0, 2.0, 1.0, 0.5, 0.25])
+    x, u0, s0, v0 = W.planted(96, 80, s_true, tag=91, return_factors=True)
+    res = H.hmat_svd(x, 32, 16, Rule("fixed_k", 8, rank_cap=8, rank_tol=1e-12))
+    ref = oracle.iterative_improvement(x, res.v, res.s, eps=1e-3, max_iters=10, rank_tol=1e-12)
+    assert ref.iterations == 1 and ref.errors[0] < 1e-13
+    assert np.allclose(ref.s, s_true, rtol=1e-12, atol=0)
+    assert oracle.principal_angle(ref.u, u0) < 1e-10 and oracle.principal_angle(ref.v, v0) < 1e-10
+
+
+def test_iterative_improvement_is_a_power_iteration_to_the_truncated_svd():
+    """From a deliberately poor V_hat (the top-k right vectors rotated 30
+    degrees into the tail) the passes converge to LAPACK's truncated SVD.
+    Each pass multiplies by X and X^T once (one power step on X^T X), so the
+    subspace error shrinks by (s_{k+1}/s_k)^2 per pass and the singular
+    values, second order in it, by (s_{k+1}/s_k)^4: the pass-to-pass Error
+    must fall at that rate."""
+    k = 6
+    s_true = np.concatenate([np.linspace(4.0, 2.0, k), 0.8 * np.linspace(1.0, 0.5, 10)])
+    x, u0, s0, v0 = W.planted(120, 90, s_true, tag=92, return_factors=True)
+    th = np.deg2rad(30.0)
+    v_start = np.cos(th) * v0[:, :k] + np.sin(th) * v0[:, k:2 * k]
+    v_start, _ = np.linalg.qr(v_start)
+    ref = oracle.iterative_improvement(x, v_start, np.full(k, 1.0), eps=1e-15, max_iters=80)
+    ut, st, vt = H.truncated_svd(x, k)
+    assert np.allclose(ref.s, st, rtol=1e-10, atol=0)
+    assert oracle.principal_angle(ref.u, ut) < 1e-8 and oracle.principal_angle(ref.v, vt) < 1e-8
+    e = np.array(ref.errors[2:12])
+    rate = np.exp(np.mean(np.diff(np.log(e))))
+    expect = (s_true[k] / s_true[k - 1]) ** 4
+    assert 0.5 * expect < rate < 1.5 * expect, (rate, expect)
+
+
+def test_iterative_improvement_stopping_rule():
+    """'while Error > eps': a huge eps stops after the first pass, eps = 0
+    runs every allowed pass."""
+    x = W.planted(64, 64, np.linspace(3, 1, 8), noise=1e-3, tag=93)
+    res = H.hmat_svd(x, 32, 32, Rule("fixed_k", 4, rank_cap=4))
+    assert oracle.iterative_improvement(x, res.v, res.s, eps=1e9, max_iters=7).iterations == 1
+    assert oracle.iterative_improvement(x, res.v, res.s, eps=0.0, max_iters=7).iterations == 7
+
+
+def test_iterative_improvement_reduces_the_mat_error():
+    """Section 4: the error against the truncated SVD drops once iterative
+    improvement is applied (here gamma truncation makes the MAT result
+    visibly inexact)."""
+    s_true = 0.9 ** np.arange(60)
+    x = W.planted(200, 160, s_true, noise=1e-4, tag=94)
+    rule = Rule("gamma", 0.05, rank_cap=64)
+    res = H.hmat_svd(x, 50, 40, rule)
+    r = res.s.size
+    ut, st, vt = H.truncated_svd(x, r)
+    xk = (ut * st) @ vt.T
+    before = H.relative_error(xk, (res.u * res.s) @ res.v.T)
+    ref = oracle.iterative_improvement(x, res.v, res.s, eps=1e-3, max_iters=20)
+    after = H.relative_error(xk, (ref.u * ref.s) @ ref.v.T)
+    assert before > 1e-4 and after < 0.8 * before, (before, after)
