@@ -149,6 +149,30 @@ hsvd_status hsvd_run(hsvd_plan_t plan, const void* const* A, const int64_t* lda,
  * must stay valid until the stream has passed the copies. */
 hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream);
 
+/* hsvd_refine -- Alg. 2 (iterative improvement) on the factors of the last
+ * hsvd_run / hsvd_run_host of this plan, in place.  Each pass computes
+ *   U_i, ., . = SVD(X V_hat);  U~, S~, V~^T = SVD(U_i^T X);
+ *   Error = max_i |S_hat_i - S~_i| / S_hat_1;  S_hat = S~, V_hat = V~,
+ *   U_hat = U_i U~
+ * for every matrix of the batch (two passes over each input), and the loop
+ * repeats while the largest Error over the batch exceeds eps, at most
+ * max_iters passes.  The paper measures Error with the spectral norm of the
+ * diagonal matrices (hence the maximum) and its listing leaves V_hat
+ * unchanged inside the loop; here V_hat takes V~ each pass (the power
+ * iteration the paper describes).  The ranks stay those of the last run (a
+ * numerically zero value drops out).
+ *
+ * The inputs read are those of the last run, through the same pointers (and,
+ * on the BF16-mixed path, the plan's BF16 copies made by that run): they must
+ * still be valid and unchanged.  Work is enqueued on `stream`, and after each
+ * pass the host waits for one small device-to-host copy of the Error values
+ * to decide the loop, so the call returns with the stream drained.
+ * iters (may be NULL): passes run.  error (may be NULL): the last Error.
+ * Returns HSVD_EINVAL (NULL plan, max_iters < 1, eps < 0 or NaN),
+ * HSVD_ENOTREADY (no run yet), HSVD_ECUDA (see hsvd_last_error). */
+hsvd_status hsvd_refine(hsvd_plan_t plan, int32_t max_iters, double eps, int32_t* iters, double* error,
+                        void* stream);
+
 /* hsvd_status_query -- read the device status words of the last run.
  * sync != 0 synchronises the plan's last stream first; with sync == 0 the
  * values may be stale.  `r` must not be NULL. */

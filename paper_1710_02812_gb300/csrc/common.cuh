@@ -173,6 +173,19 @@ struct EnergyTask {
 template <class TA, class TO>
 cudaError_t launch_block_energy(const EnergyTask* tasks, int ntasks, const MatRef* mats, cudaStream_t s);
 
+// One pass of Alg. 2 ends by measuring Error = max_i |sig_i - snew_i| / sig_1
+// (into *err) and replacing sig, rank by snew, rnew.
+template <class T>
+struct RefineTask {
+  T* sig;
+  const T* snew;
+  int* rank;
+  const int* rnew;
+  int kcap;
+  double* err;
+};
+template <class T>
+cudaError_t launch_refine_update(const RefineTask<T>* tasks, int ntasks, cudaStream_t s);
 // Copy a row-major factor (h x rank, ld) into a column-major destination
 // (ldd), flipping column signs so the largest |entry| of each U column is
 // positive (the same flips applied to the paired V column).

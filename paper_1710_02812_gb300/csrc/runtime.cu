@@ -95,6 +95,8 @@ struct PlanImpl {
   std::vector<Blob> blobs;
   std::vector<Step> steps;
   std::vector<Step> init_steps;
+  std::vector<Step> refine_steps;  // one pass of Alg. 2 over every matrix (hsvd_refine)
+  double* refine_err = nullptr;    // per matrix: Error of the last pass (device)
   std::vector<ProblemOut> outs;
   bool ran = false;
   cudaStream_t last_stream = nullptr;
@@ -1121,6 +1123,116 @@ struct Builder {
         tag(7, 1, kc, 0, (double)(mu + mv) * kc * sizeof(T));
       }
     }
+
+    // ---------------------------------------------------- Alg. 2, one pass
+    // Run by hsvd_refine on the factors of the last run, in place:
+    //   X V_hat = Q_y R_y, R_y = A S B^T   => U_i = Q_y A          (SVD(X V_hat))
+    //   X^T U_i = Q_z R_z, R_z = C S D^T   => U_i^T X = D S (Q_z C)^T
+    //   U_hat = U_i D, Sigma_hat = S, V_hat = Q_z C                 (SVD(U_i^T X))
+    // and Error = max |Sigma_old - Sigma_hat| / sigma_old_1.
+    std::swap(P.steps, P.refine_steps);
+    {
+      std::vector<InputOp> ops1, ops2;
+      std::vector<OrthW> owy, owz;
+      std::vector<JacobiTask<T>> j1, j2;
+      std::vector<GS> gi, gv, gu;
+      std::vector<RefineTask<T>> rt;
+      TruncParams tpf = tp;
+      tpf.mode = 0;
+      tpf.param = kc;
+      double* errs = alloc<double>((size_t)P.batch);
+      if (base_real()) P.refine_err = errs;
+      for (int b = 0; b < P.batch; ++b) {
+        const ProblemOut po = P.outs[b];
+        const int mm = po.mm, nn = po.nn;
+        T* Uf = static_cast<T*>(po.U);
+        T* Vf = static_cast<T*>(po.V);
+        T* sf = static_cast<T*>(po.sig);
+        int* rf = po.rank;
+        const Dim kv = dimd(kc, rf);
+        T* Y = alloc<T>((size_t)mm * kc);
+        T* Qy = alloc<T>((size_t)mm * kc);
+        T* Ry = alloc<T>((size_t)kc * kc);
+        T* A = alloc<T>((size_t)kc * kc);
+        T* s1 = alloc<T>(kc);
+        int* r1 = alloc<int>(1);
+        T* Ui = alloc<T>((size_t)mm * kc);
+        T* Z = alloc<T>((size_t)nn * kc);
+        T* Qz = alloc<T>((size_t)nn * kc);
+        T* Rz = alloc<T>((size_t)kc * kc);
+        T* C = alloc<T>((size_t)kc * kc);
+        T* D = alloc<T>((size_t)kc * kc);
+        T* s2 = alloc<T>(kc);
+        int* r2 = alloc<int>(1);
+        ops1.push_back(input_op(false, b, po.trans, 0, 0, mm, nn, Vf, kc, kv, Y, kc));
+        owy.push_back(orth_bufs(Y, kc, mm, kv, kc, true, Qy, Ry));
+        JacobiTask<T> a = jblank();
+        a.load = 0;
+        a.src = Ry;
+        a.rs = kc;
+        a.cs = 1;
+        a.nr = kv;
+        a.nc = kv;
+        a.U = A;
+        a.ldu = kc;
+        a.ucap = kc;
+        a.sig = s1;
+        a.rank = r1;
+        j1.push_back(a);
+        const Dim k1 = dimd(kc, r1);
+        gi.push_back(nn_(Qy, kc, mm, kv, A, kc, k1, Ui, kc));
+        ops2.push_back(input_op(true, b, po.trans, 0, 0, mm, nn, Ui, kc, k1, Z, kc));
+        owz.push_back(orth_bufs(Z, kc, nn, k1, kc, true, Qz, Rz));
+        JacobiTask<T> c = jblank();
+        c.load = 0;
+        c.src = Rz;
+        c.rs = kc;
+        c.cs = 1;
+        c.nr = k1;
+        c.nc = k1;
+        c.U = C;
+        c.ldu = kc;
+        c.ucap = kc;
+        c.V = D;
+        c.ldv = kc;
+        c.sig = s2;
+        c.rank = r2;
+        j2.push_back(c);
+        const Dim k2 = dimd(kc, r2);
+        gv.push_back(nn_(Qz, kc, nn, k1, C, kc, k2, Vf, kc));
+        gu.push_back(nn_(Ui, kc, mm, k1, D, kc, k2, Uf, kc));
+        rt.push_back(RefineTask<T>{sf, s2, rf, r2, kc, errs + b});
+      }
+      emit_input("refine.XV", ops1, true);
+      emit_orth("refine.orthY", owy, 2, kc);
+      emit_jacobi("refine.coreY", j1, kc, kc, false, tpf);
+      emit_gemm("refine.Ui", gi, false);
+      emit_input("refine.XtU", ops2, true);
+      emit_orth("refine.orthZ", owz, 2, kc);
+      emit_jacobi("refine.coreZ", j2, kc, kc, true, tpf);
+      emit_gemm("refine.V", gv, false);
+      emit_gemm("refine.U", gu, false);
+      PlanImpl* p = &P;
+      const size_t brt = P.add_blob(rt);
+      const int nrt = (int)rt.size();
+      P.steps.push_back(Step{"refine.error", [p, brt, nrt](cudaStream_t s) {
+                               return launch_refine_update<T>(p->table<RefineTask<T>>(brt), nrt, s);
+                             }});
+      tag(6, nrt, kc, 0, (double)nrt * kc * 2 * sizeof(T));
+      for (int b = 0; b < P.batch; ++b) {
+        const ProblemOut po = P.outs[b];
+        T* su = static_cast<T*>(po.trans ? po.V : po.U);
+        T* sv = static_cast<T*>(po.trans ? po.U : po.V);
+        const int mu = po.trans ? po.nn : po.mm;
+        const int mv = po.trans ? po.mm : po.nn;
+        const int* rk = po.rank;
+        P.steps.push_back(Step{"refine.signs", [su, sv, mu, mv, rk, kc](cudaStream_t s) {
+                                 return launch_sign_normalise<T>(su, kc, mu, sv, kc, mv, rk, kc, s);
+                               }});
+        tag(7, 1, kc, 0, (double)(mu + mv) * kc * sizeof(T));
+      }
+    }
+    std::swap(P.steps, P.refine_steps);
   }
 
   GS nn_(const T* A, int64_t lda, int M, Dim K, const T* B, int64_t ldb, Dim N, T* C, int64_t ldc) {
@@ -1137,6 +1249,7 @@ hsvd_status build_plan(PlanImpl& P) {
   }
   P.steps.clear();
   P.init_steps.clear();
+  P.refine_steps.clear();
   P.blobs.clear();
   P.outs.clear();
   P.tmaps.clear();
@@ -1451,6 +1564,41 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
     dld[b] = P.n[b];
   }
   return run_impl(plan, dptr.data(), dld.data(), s);
+}
+
+hsvd_status hsvd_refine(hsvd_plan_t plan, int32_t max_iters, double eps, int32_t* iters, double* error,
+                        void* stream) {
+  if (!plan || max_iters < 1 || !(eps >= 0.0)) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (!P.ran) return HSVD_ENOTREADY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<double> err(P.batch, 0.0);
+  double worst = 0.0;
+  int done = 0;
+  P.last_error.clear();
+  while (done < max_iters) {
+    for (size_t i = 0; i < P.refine_steps.size(); ++i) {
+      const cudaError_t e = P.refine_steps[i].run(s);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        P.last_error = P.refine_steps[i].name + ": " + cudaGetErrorString(e);
+        return HSVD_ECUDA;
+      }
+    }
+    ++done;
+    // the loop condition of Alg. 2 is decided on the host: one small read
+    if (cudaMemcpyAsync(err.data(), P.refine_err, sizeof(double) * P.batch, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return HSVD_ECUDA;
+    worst = 0.0;
+    for (double v : err) worst = std::max(worst, v);
+    if (!(worst > eps)) break;  // a NaN error also stops (status reports it)
+  }
+  P.last_stream = s;
+  if (iters) *iters = done;
+  if (error) *error = worst;
+  return HSVD_OK;
 }
 
 hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r) {

@@ -1739,6 +1739,35 @@ cudaError_t launch_block_energy(const EnergyTask* tasks, int ntasks, const MatRe
   return cudaGetLastError();
 }
 
+namespace {
+template <class T>
+__global__ void __launch_bounds__(256) k_refine_update(const RefineTask<T>* __restrict__ tasks) {
+  const RefineTask<T> tk = tasks[blockIdx.x];
+  if (threadIdx.x == 0) {
+    const int r0 = *tk.rank, r1 = *tk.rnew, r = max(r0, r1);
+    const double s1 = r0 > 0 ? (double)tk.sig[0] : 0.0;
+    double mx = 0.0;
+    for (int i = 0; i < r; ++i) {
+      const double a = i < r0 ? (double)tk.sig[i] : 0.0, b = i < r1 ? (double)tk.snew[i] : 0.0;
+      mx = fmax(mx, fabs(a - b));
+    }
+    *tk.err = s1 > 0.0 ? mx / s1 : 0.0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < tk.kcap; c += blockDim.x) tk.sig[c] = tk.snew[c];
+  if (threadIdx.x == 0) *tk.rank = *tk.rnew;
+}
+}  // namespace
+
+template <class T>
+cudaError_t launch_refine_update(const RefineTask<T>* tasks, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_refine_update<T><<<ntasks, 256, 0, s>>>(tasks);
+  return cudaGetLastError();
+}
+template cudaError_t launch_refine_update<float>(const RefineTask<float>*, int, cudaStream_t);
+template cudaError_t launch_refine_update<double>(const RefineTask<double>*, int, cudaStream_t);
+
 template <class T>
 cudaError_t launch_sign_normalise(T* U, int64_t ldu, int m, T* V, int64_t ldv, int n, const int* rank, int kcap,
                                   cudaStream_t s) {

@@ -26,7 +26,8 @@ WHERE = {"host": 0, "device": 1}
 EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd_factors",
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
-            "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error")
+            "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error",
+            "hsvd_refine")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -103,6 +104,8 @@ def lib():
         L.hsvd_block_svd_noalloc.restype = ctypes.c_int
         L.hsvd_last_error.argtypes = [P]
         L.hsvd_last_error.restype = ctypes.c_char_p
+        L.hsvd_refine.argtypes = [P, i32, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), P]
+        L.hsvd_refine.restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -161,6 +164,15 @@ def hsvd_run_host(plan, ptrs: Sequence[int], lda: Sequence[int], stream=None):
     code = lib().hsvd_run_host(plan, arr, ld, _stream_ptr(stream))
     if code != HSVD_OK:
         raise HsvdError(code, "hsvd_run_host" + _detail(plan))
+
+
+def hsvd_refine(plan, max_iters: int, eps: float, stream=None):
+    it, err = ctypes.c_int32(), ctypes.c_double()
+    code = lib().hsvd_refine(plan, int(max_iters), float(eps), ctypes.byref(it), ctypes.byref(err),
+                             _stream_ptr(stream))
+    if code != HSVD_OK:
+        raise HsvdError(code, "hsvd_refine" + _detail(plan))
+    return it.value, err.value
 
 
 def hsvd_last_error(plan) -> str:
@@ -324,6 +336,10 @@ class Plan:
                             self.n[idx], WHERE["device"], _stream_ptr(stream))
         _check(code, "hsvd_factors")
         return r.value
+
+    def refine(self, max_iters=3, eps=1e-3, stream=None):
+        """Alg. 2 on the last run's factors, in place; returns (passes, Error)."""
+        return hsvd_refine(self._h, max_iters, eps, stream)
 
     def status(self, sync=True):
         return hsvd_status_query(self._h, sync)

@@ -323,3 +323,60 @@ def test_fp32_wide_cores_on_clusters(m, n, br, bc, k):
     assert st["not_converged"] == 0 and st["nonfinite"] == 0
     ref = oracle_run(x, br, bc, "fixed_k", k, "f32")
     check(x, got, ref, "f32", f"clusters {m}x{n}/{br}", s_true=s_true)
+
+
+# ---------------------------------------------------------------- Alg. 2 (iterative improvement)
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16_mixed"])
+def test_refine_matches_oracle_alg2(prec):
+    """hsvd_refine runs the passes of Alg. 2 on the last run's factors; after
+    the same number of passes it matches the oracle's Alg. 2 started from
+    the oracle's own MAT result (both contract toward the truncated SVD)."""
+    k = 12
+    s_true = np.concatenate([np.linspace(4.0, 2.0, k), 0.8 * 0.9 ** np.arange(40)])
+    x = W.planted(700, 520, s_true, noise=1e-6, tag=101)
+    if prec == "bf16_mixed":
+        x = W.bf16_round(x.astype(np.float32))
+    xin = x if prec == "f64" else x.astype(np.float32)
+    passes = 8 if prec == "f64" else 4
+    plan = hsvd.Plan(700, 520, 128, 128, "fixed_k", k, prec=prec)
+    with pytest.raises(hsvd.HsvdError):
+        plan.refine(1, 0.0)                                    # no run yet: ENOTREADY
+    plan.run([to_device(xin, prec)])
+    it, err = plan.refine(passes, 0.0)
+    assert it == passes and err >= 0.0
+    got = plan.factors(0)
+    st = plan.status()
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0
+    res = oracle_run(xin, 128, 128, "fixed_k", k, prec)
+    ref = oracle.iterative_improvement(np.asarray(xin, np.float64), res.v, res.s, eps=0.0, max_iters=passes,
+                                       rank_tol=RANK_TOL[prec])
+    check(xin, got, ref, prec, f"refine {prec}", s_true=s_true)
+    # both sit on the truncated SVD (the power iteration's fixed point)
+    ut, stt, vt = H.truncated_svd(np.asarray(xin, np.float64), k)
+    assert oracle.sigma_rel_err(got[1], stt, k) <= TOL[prec][0]
+
+
+def test_refine_stopping_rule_and_error_drop():
+    """'while Error > eps': a huge eps stops after one pass, eps = 0 runs
+    them all; on a gamma-truncated result the error against the truncated
+    SVD drops (Section 4)."""
+    s_true = 0.9 ** np.arange(60)
+    x = W.planted(400, 320, s_true, noise=1e-4, tag=102).astype(np.float32)
+    plan = hsvd.Plan(400, 320, 100, 80, "gamma", 0.05, rank_cap=64, prec="f32", power_iters=4)
+    xd = torch.from_numpy(x).cuda()
+    plan.run([xd])
+    u0, s0, v0 = plan.factors(0)
+    r = s0.size
+    ut, st, vt = H.truncated_svd(x.astype(np.float64), r)
+    xk = (ut * st) @ vt.T
+    before = H.relative_error(xk, (u0.astype(np.float64) * s0) @ v0.T.astype(np.float64))
+    assert plan.refine(5, 1e9)[0] == 1
+    plan.run([xd])
+    it, err = plan.refine(20, 1e-3)
+    assert 1 <= it <= 20 and (err <= 1e-3 or it == 20)
+    u1, s1, v1 = plan.factors(0)
+    after = H.relative_error(xk, (u1.astype(np.float64) * s1) @ v1.T.astype(np.float64))
+    assert before > 1e-4 and after < 0.8 * before, (before, after)
+    plan.run([xd])
+    assert plan.refine(4, 0.0)[0] == 4
