@@ -39,6 +39,9 @@ K = 64
 MODES = 512
 NOISE = 1e-5
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+# DRAM bytes per 128 x 128 core of k_jacobi_bp (ncu dram__bytes_read + dram__bytes_write of one
+# merge-level launch of the 2048^2 case: 472064 bytes for 8 cores)
+JACOBI_DRAM_BYTES_PER_CORE = 472064 / 8
 
 
 def workload_config(prec, q):
@@ -235,11 +238,14 @@ def run_ours(args, world, rank, local):
         cpu_base = {"value": M * N * 4 / t_oracle / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
                     "sample": f"full {M}x{N} matrix, 1 run ({t_oracle:.1f} s, numpy/LAPACK FP64)"}
 
-    # ---- warm-up, then K timed steps with per-step events
+    # ---- warm-up, then K timed steps; CUDA events around the core-SVD
+    # (Jacobi) launches only, the dominant family, inside the timed region
+    # (events around every step add ~1 ms per step: the per-family split is
+    # taken in a separate instrumented pass below)
     for _ in range(args.warmup):
         plan.run([xd])
     torch.cuda.synchronize(dev)
-    plan.set_timing(True)
+    plan.set_timing(2)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -256,6 +262,10 @@ def run_ours(args, world, rank, local):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_max(world, ms, dev)
+    jac_ms, jac_runs = plan.step_times()
+    plan.set_timing(1)                       # instrumented pass: every step
+    for _ in range(min(args.steps, 5)):
+        plan.run([xd], stream=stream)
     step_ms, runs = plan.step_times()
     plan.set_timing(False)
     steps = plan.steps()
@@ -287,11 +297,14 @@ def run_ours(args, world, rank, local):
     dom = max(fam, key=lambda k: fam[k]["ms"])
     pk, pk_src = peaks()
     d = fam[dom]
+    jac_live = sum(t for info, t in zip(steps, jac_ms) if info["kind"] == "jacobi") / max(1, jac_runs)
     if dom == "jacobi":
+        d = dict(d, ms=jac_live)          # the timed region's own events
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roof = {"kernel": "k_jacobi (one-sided Jacobi core SVD)", "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None,
+                "traffic": JACOBI_DRAM_BYTES_PER_CORE * st["jacobi_cores"] / max(1, d["launches"]),
+                "traffic_source": "ncu DRAM bytes per core (2048^2 merge level) x cores per launch",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "work": "22 n^3 flops per n x n core (Section 3.1 count)"}
     elif dom == "gemm_tc":
@@ -308,7 +321,10 @@ def run_ours(args, world, rank, local):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "peak_source": "derived FP32 peak"}
-    roof["share_of_step"] = d["ms"] / max(1e-9, sum(f["ms"] for f in fam.values()))
+    roof["share_of_step"] = d["ms"] / ms
+    roof["launches_per_step"] = d["launches"]
+    roof["timing"] = ("CUDA events around each launch of the family inside the timed region"
+                      if dom == "jacobi" else "instrumented pass (events around every step)")
 
     # ---- the other side of "mixed vs plain FP32": same workload, FP32 path
     compare = None
@@ -342,6 +358,7 @@ def run_ours(args, world, rank, local):
             "config": workload_config(args.prec, q),
             "roofline": roof,
             "kernel_families_ms": {k: round(v["ms"], 4) for k, v in sorted(fam.items(), key=lambda kv: -kv[1]["ms"])},
+            "kernel_families_note": "instrumented pass after the timed region: events around every step",
             "e2e": {"value": world * M * N * 4 / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": plan.launches_per_run * args.steps,

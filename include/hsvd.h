@@ -220,8 +220,11 @@ int32_t hsvd_step_count(hsvd_plan_t plan);
 hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* kind,
                            int32_t* tasks, int32_t* dim, double* flops, double* bytes);
 
-/* hsvd_set_timing -- on != 0: record events around every step of the
- * following runs; resets the accumulated times. */
+/* hsvd_set_timing -- per-step device times of the following runs (CUDA
+ * events on the run's stream): on = 1 around every step, on = 2 around the
+ * core-SVD (Jacobi) steps only (two events per such step, little overhead;
+ * the other steps report 0), on = 0 off.  Resets the accumulated times.
+ * Timed runs launch step by step (no CUDA graph).  EINVAL for other values. */
 hsvd_status hsvd_set_timing(hsvd_plan_t plan, int32_t on);
 
 /* hsvd_step_times -- synchronise on the timed runs enqueued so far and

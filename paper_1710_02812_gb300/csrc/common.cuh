@@ -81,6 +81,8 @@ struct GemmItem {
 // FP64 64 x 64.  Items and split-K partial buffers are laid out in tiles.
 constexpr int gemm_tile_m(size_t acc_elem) { return acc_elem == 4 ? 128 : 64; }
 constexpr int GEMM_TILE_N = 64;
+// FP32 split-K reduction: CTAs per 128 x 64 output tile (GemmItem.kc picks the rows)
+constexpr int GEMM_REDUCE_PARTS = 8;
 
 // ---------------------------------------------------------------- small tasks
 // Cholesky of a k x k Gram matrix G with relative pivot dropping, returning

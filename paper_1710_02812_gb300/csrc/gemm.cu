@@ -419,6 +419,8 @@ __global__ void __launch_bounds__(256) k_gemm2(const GemmTask<TA, float, float>*
 template <class TA>
 __global__ void __launch_bounds__(256) k_gemm2_reduce(const GemmTask<TA, float, float>* __restrict__ tasks,
                                                       const GemmItem* __restrict__ items) {
+  // item.kc selects 16 of the tile's 128 rows: 8 CTAs share a tile, each
+  // thread sums one float4 of the tile over the chunks, in chunk order
   const GemmItem it = items[blockIdx.x];
   const GemmTask<TA, float, float>& tk = tasks[it.task];
   const int M = eff(tk.M), N = eff(tk.N);
@@ -426,15 +428,26 @@ __global__ void __launch_bounds__(256) k_gemm2_reduce(const GemmTask<TA, float, 
   if (m0 >= M || n0 >= N) return;
   const int64_t tile_stride = (int64_t)tk.mtiles * tk.ntiles * (BM2 * BN2);
   const float* P = tk.partial + ((int64_t)it.mt * tk.ntiles + it.nt) * (BM2 * BN2);
-  for (int e = threadIdx.x; e < BM2 * BN2; e += 256) {
-    const int r = e / BN2, c = e % BN2;
-    const int gm = m0 + r, gn = n0 + c;
-    if (gm >= M || gn >= N) continue;
-    float sacc = 0.f;
-    for (int kc = 0; kc < tk.nkc; ++kc) sacc += P[kc * tile_stride + e];
-    float v = tk.alpha * sacc;
-    if (tk.C0) v += tk.beta * tk.C0[(int64_t)gm * tk.ldc0 + gn];
-    tk.C[(int64_t)gm * tk.ldc + gn] = v;
+  static_assert(BM2 / GEMM_REDUCE_PARTS * BN2 / 4 == 256, "one float4 per thread");
+  const int e = (it.kc * (BM2 / GEMM_REDUCE_PARTS)) * BN2 + 4 * threadIdx.x;
+  const int r = e / BN2, c = e % BN2;
+  const int gm = m0 + r, gn = n0 + c;
+  if (gm >= M || gn >= N) return;
+  const float4* p4 = reinterpret_cast<const float4*>(P + e);
+  const int64_t st4 = tile_stride / 4;
+  float4 acc = p4[0];
+  for (int kc = 1; kc < tk.nkc; ++kc) {
+    const float4 v = p4[kc * st4];
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+  }
+  const float sv[4] = {acc.x, acc.y, acc.z, acc.w};
+  for (int q = 0; q < 4 && gn + q < N; ++q) {
+    float v = tk.alpha * sv[q];
+    if (tk.C0) v += tk.beta * tk.C0[(int64_t)gm * tk.ldc0 + gn + q];
+    tk.C[(int64_t)gm * tk.ldc + gn + q] = v;
   }
 }
 

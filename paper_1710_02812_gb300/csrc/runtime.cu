@@ -32,6 +32,17 @@ constexpr int KCHUNK = 2048;
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// SMs of the current device (152 on GB300 if the query fails).
+inline int num_sms() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  return v > 0 ? v : 152;
+}
+
 struct Blob {
   std::vector<char> bytes;
   size_t dev_off = 0;
@@ -40,6 +51,7 @@ struct Blob {
 struct Step {
   std::string name;
   std::function<cudaError_t(cudaStream_t)> run;
+  bool varies = false;  // its launch arguments change from run to run (kept out of the graph)
   int kind = 0;   // hsvd_step_kind
   int tasks = 0;  // tasks (blocks / merges / slabs / matrices) in the launch
   int dim = 0;    // core dimension (Jacobi, Cholesky) or columns (GEMMs)
@@ -101,13 +113,26 @@ struct PlanImpl {
   bool ran = false;
   cudaStream_t last_stream = nullptr;
   int launches_per_run = 0;
-  bool timing = false;  // record an event after every step of every run
+  int timing = 0;  // 1: events around every step of every run; 2: around the core-SVD steps only
   std::vector<std::vector<cudaEvent_t>> pending, pool;  // event sets of timed runs
+  std::vector<std::vector<char>> pending_rec;            // which events of a pending set were recorded
   std::vector<double> step_ms;  // per-step device time summed over collected runs
   int timed_runs = 0;
   int dev = 0;
 
+  // CUDA graph of the steps after the run-dependent prefix (captured on the
+  // first untimed run, replayed afterwards); graph_off after a failed capture
+  // or with HSVD_NO_GRAPH set.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  bool graph_off = false;
+  size_t graph_from = 0;  // first step inside the graph
+
   ~PlanImpl() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (arena) cudaFree(arena);
     if (tables) cudaFree(tables);
     if (d_mats) cudaFree(d_mats);
@@ -125,9 +150,16 @@ struct PlanImpl {
   // on the last event of each).
   void collect_timing() {
     if (step_ms.size() != steps.size()) step_ms.assign(steps.size(), 0.0);
-    for (auto& v : pending) {
-      cudaEventSynchronize(v.back());
+    for (size_t r = 0; r < pending.size(); ++r) {
+      auto& v = pending[r];
+      const auto& rec = pending_rec[r];
+      for (size_t i = v.size(); i-- > 0;)
+        if (rec[i]) {
+          cudaEventSynchronize(v[i]);  // the last event recorded by that run
+          break;
+        }
       for (size_t i = 0; i + 1 < v.size(); ++i) {
+        if (!rec[i] || !rec[i + 1]) continue;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, v[i], v[i + 1]);
         step_ms[i] += ms;
@@ -136,6 +168,7 @@ struct PlanImpl {
       pool.push_back(std::move(v));
     }
     pending.clear();
+    pending_rec.clear();
   }
 
   template <class X>
@@ -256,6 +289,14 @@ struct Builder {
   template <class G>
   void finish_items(std::vector<G>& tasks, bool is_tn, std::vector<GemmItem>& items, std::vector<GemmItem>& red) {
     constexpr int TM = gemm_tile_m(sizeof(T)), TN = GEMM_TILE_N;
+    // Output tiles of the whole launch: when they are fewer than two per SM,
+    // K is split so the launch fills the GPU and each CTA's sequential K loop
+    // stays short (a 64 x 64 product over K = 512 in one CTA is bound by the
+    // latency of its 32 K steps); chunks are multiples of 64 and at least 128.
+    int64_t tiles = 0;
+    for (const auto& g : tasks)
+      if (g.M.cap > 0 && g.N.cap > 0) tiles += (int64_t)cdiv(g.M.cap, TM) * cdiv(g.N.cap, TN);
+    const int64_t target = 2 * (int64_t)num_sms();
     for (size_t t = 0; t < tasks.size(); ++t) {
       G& g = tasks[t];
       g.mtiles = cdiv(g.M.cap, TM);
@@ -265,14 +306,17 @@ struct Builder {
       g.partial = nullptr;
       if (g.M.cap <= 0 || g.N.cap <= 0) continue;
       const int ktot = g.K.cap + (is_tn ? 0 : g.K2.cap);
-      // long K with few output tiles: split finer so the launch fills the GPU
-      const int chunk = (ktot > KCHUNK && g.mtiles * g.ntiles <= 2) ? KCHUNK / 4 : KCHUNK;  // 512 or 2048
+      int64_t split = std::max<int64_t>(cdiv(ktot, KCHUNK), tiles > 0 ? (target + tiles - 1) / tiles : 1);
+      split = std::min<int64_t>(split, std::max(1, ktot / 128));
+      const int chunk = (int)(((ktot + split - 1) / split + 63) / 64 * 64);
       if (ktot > chunk) {
         g.kchunk = chunk;
         g.nkc = cdiv(ktot, chunk);
         g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * TM * TN);
+        const int parts = sizeof(T) == 4 ? GEMM_REDUCE_PARTS : 1;  // FP64 reduces a tile per CTA
         for (int mt = 0; mt < g.mtiles; ++mt)
-          for (int nt = 0; nt < g.ntiles; ++nt) red.push_back(GemmItem{(int)t, mt, nt, 0});
+          for (int nt = 0; nt < g.ntiles; ++nt)
+            for (int q = 0; q < parts; ++q) red.push_back(GemmItem{(int)t, mt, nt, q});
       }
       for (int kc = 0; kc < g.nkc; ++kc)
         for (int mt = 0; mt < g.mtiles; ++mt)
@@ -875,6 +919,7 @@ struct Builder {
                                }
                                return cudaSuccess;
                              }});
+      P.steps.back().varies = true;
       double by = 0;
       for (int b = 0; b < P.batch; ++b) by += (double)P.m[b] * P.n[b] * (P.in_elem + (P.use_tc ? 4 : 2));
       tag(9, P.batch, 0, 0, by);
@@ -1429,6 +1474,7 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   // Tensor-core products need the block origins on 8-element (16-byte)
   // boundaries for TMA, a sketch of at most 256 columns, and the tensor-map
   // encoder of the driver.
+  P.graph_off = std::getenv("HSVD_NO_GRAPH") != nullptr;
   P.use_tc = P.mixed && block_rows % 8 == 0 && block_cols % 8 == 0 && P.kp <= 256 && !std::getenv("HSVD_NO_TC") &&
              hsvd::tc_available();
   if (P.host_staging) {
@@ -1484,10 +1530,78 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
       for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return HSVD_ECUDA;
     }
+  }
+  std::vector<char> rec(timed ? P.steps.size() + 1 : 0, 0);
+  const bool all_steps = trace || P.timing == 1;
+  if (timed && all_steps) {
     cudaEventRecord(ev[0], s);
+    rec[0] = 1;
   }
   P.last_error.clear();
+  if (!timed && !P.graph_off) {
+    // Run-dependent prefix (the input conversion reads the caller's
+    // pointers), then one launch of the graph of every later step.
+    size_t i = 0;
+    for (; i < P.steps.size() && P.steps[i].varies; ++i) {
+      const cudaError_t err = P.steps[i].run(s);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        P.last_error = P.steps[i].name + ": " + cudaGetErrorString(err);
+        return HSVD_ECUDA;
+      }
+    }
+    if (!P.graph_exec) {
+      // captured on a private stream (the caller's may be the legacy default
+      // stream, which cannot be captured); nothing executes during capture
+      P.graph_from = i;
+      bool ok = P.cap_stream || cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      const bool capturing = ok;
+      for (size_t j = i; ok && j < P.steps.size(); ++j)
+        if (P.steps[j].varies || P.steps[j].run(P.cap_stream) != cudaSuccess) ok = false;
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = capturing ? cudaStreamEndCapture(P.cap_stream, &g) : cudaErrorUnknown;
+      ok = ok && ec == cudaSuccess && g != nullptr &&
+           cudaGraphInstantiate(&P.graph_exec, g, 0) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        P.graph_exec = nullptr;
+        P.graph_off = true;  // launch step by step from now on
+      } else {
+        P.graph = g;
+      }
+    }
+    if (P.graph_exec) {
+      if (P.graph_from != i) return HSVD_ECUDA;
+      const cudaError_t err = cudaGraphLaunch(P.graph_exec, s);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        P.last_error = std::string("graph launch: ") + cudaGetErrorString(err);
+        return HSVD_ECUDA;
+      }
+      P.ran = true;
+      P.last_stream = s;
+      return HSVD_OK;
+    }
+    for (; i < P.steps.size(); ++i) {
+      const cudaError_t err = P.steps[i].run(s);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        P.last_error = P.steps[i].name + ": " + cudaGetErrorString(err);
+        return HSVD_ECUDA;
+      }
+    }
+    P.ran = true;
+    P.last_stream = s;
+    return HSVD_OK;
+  }
   for (size_t i = 0; i < P.steps.size(); ++i) {
+    const bool mark = timed && (all_steps || P.steps[i].kind == 5);
+    if (mark && !rec[i]) {
+      cudaEventRecord(ev[i], s);
+      rec[i] = 1;
+    }
     const cudaError_t err = P.steps[i].run(s);
     if (err != cudaSuccess) {
       cudaGetLastError();
@@ -1495,9 +1609,15 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
       if (timed) P.pool.push_back(std::move(ev));
       return HSVD_ECUDA;
     }
-    if (timed) cudaEventRecord(ev[i + 1], s);
+    if (mark) {
+      cudaEventRecord(ev[i + 1], s);
+      rec[i + 1] = 1;
+    }
   }
-  if (timed) P.pending.push_back(std::move(ev));
+  if (timed) {
+    P.pending.push_back(std::move(ev));
+    P.pending_rec.push_back(std::move(rec));
+  }
   if (trace) {
     // Per-step device time of this run, summed by step name without the
     // tree level, printed to stderr.
@@ -1740,8 +1860,9 @@ hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name
 hsvd_status hsvd_set_timing(hsvd_plan_t plan, int32_t on) {
   if (!plan) return HSVD_EINVAL;
   PlanImpl& P = plan->impl;
+  if (on < 0 || on > 2) return HSVD_EINVAL;
   P.collect_timing();
-  P.timing = on != 0;
+  P.timing = on;
   P.step_ms.assign(P.steps.size(), 0.0);
   P.timed_runs = 0;
   return HSVD_OK;

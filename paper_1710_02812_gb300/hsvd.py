@@ -220,8 +220,10 @@ def hsvd_step_info(plan, i: int) -> dict:
             "dim": dim.value, "flops": fl.value, "bytes": by.value}
 
 
-def hsvd_set_timing(plan, on: bool):
-    _check(lib().hsvd_set_timing(plan, 1 if on else 0), "hsvd_set_timing")
+def hsvd_set_timing(plan, on):
+    """on: False/0 off, True/1 every step, 2 core-SVD steps only."""
+    mode = on if (isinstance(on, int) and not isinstance(on, bool)) else (1 if on else 0)
+    _check(lib().hsvd_set_timing(plan, mode), "hsvd_set_timing")
 
 
 def hsvd_step_times(plan):
