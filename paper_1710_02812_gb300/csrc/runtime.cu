@@ -116,6 +116,7 @@ struct PlanImpl {
   int timing = 0;  // 1: events around every step of every run; 2: around the core-SVD steps only
   std::vector<std::vector<cudaEvent_t>> pending, pool;  // event sets of timed runs
   std::vector<std::vector<char>> pending_rec;            // which events of a pending set were recorded
+  std::vector<char> pending_owned;                       // 0: the timing graph's fixed events (no pool)
   std::vector<double> step_ms;  // per-step device time summed over collected runs
   int timed_runs = 0;
   int dev = 0;
@@ -126,12 +127,22 @@ struct PlanImpl {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  // timing mode 2 with graphs: a second graph with event-record nodes around
+  // the core-SVD steps; its events hold the last replay's times
+  cudaGraph_t tgraph = nullptr;
+  cudaGraphExec_t tgraph_exec = nullptr;
+  std::vector<cudaEvent_t> tev;
+  std::vector<char> trec;
   bool graph_off = false;
   size_t graph_from = 0;  // first step inside the graph
 
   ~PlanImpl() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (graph) cudaGraphDestroy(graph);
+    if (tgraph_exec) cudaGraphExecDestroy(tgraph_exec);
+    if (tgraph) cudaGraphDestroy(tgraph);
+    for (auto e : tev)
+      if (e) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (arena) cudaFree(arena);
     if (tables) cudaFree(tables);
@@ -165,10 +176,11 @@ struct PlanImpl {
         step_ms[i] += ms;
       }
       ++timed_runs;
-      pool.push_back(std::move(v));
+      if (pending_owned[r]) pool.push_back(std::move(v));
     }
     pending.clear();
     pending_rec.clear();
+    pending_owned.clear();
   }
 
   template <class X>
@@ -1596,6 +1608,71 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
     P.last_stream = s;
     return HSVD_OK;
   }
+  if (timed && !all_steps && !P.graph_off && !P.tgraph_exec) {
+    // capture the timing graph: the steps after the run-dependent prefix,
+    // with event-record nodes around the core-SVD steps
+    size_t i = 0;
+    while (i < P.steps.size() && P.steps[i].varies) ++i;
+    bool ok = P.cap_stream || cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    P.tev.assign(P.steps.size() + 1, nullptr);
+    P.trec.assign(P.steps.size() + 1, 0);
+    for (size_t j = i; ok && j < P.steps.size(); ++j)
+      if (P.steps[j].kind == 5)
+        for (size_t q : {j, j + 1})
+          if (!P.tev[q]) ok = ok && cudaEventCreate(&P.tev[q]) == cudaSuccess;
+    ok = ok && cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const bool capturing = ok;
+    for (size_t j = i; ok && j < P.steps.size(); ++j) {
+      const bool mark = P.steps[j].kind == 5;
+      if (mark && !P.trec[j]) {
+        // External: a real event-record node (a plain record during capture
+        // only expresses a dependency inside the graph)
+        ok = cudaEventRecordWithFlags(P.tev[j], P.cap_stream, cudaEventRecordExternal) == cudaSuccess;
+        P.trec[j] = 1;
+      }
+      if (ok && (P.steps[j].varies || P.steps[j].run(P.cap_stream) != cudaSuccess)) ok = false;
+      if (ok && mark) {
+        ok = cudaEventRecordWithFlags(P.tev[j + 1], P.cap_stream, cudaEventRecordExternal) == cudaSuccess;
+        P.trec[j + 1] = 1;
+      }
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = capturing ? cudaStreamEndCapture(P.cap_stream, &g) : cudaErrorUnknown;
+    ok = ok && ec == cudaSuccess && g != nullptr && cudaGraphInstantiate(&P.tgraph_exec, g, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      P.tgraph_exec = nullptr;
+      P.graph_off = true;  // step by step from now on
+    } else {
+      P.tgraph = g;
+      P.graph_from = i;
+    }
+  }
+  if (timed && !all_steps && P.tgraph_exec) {
+    P.pool.push_back(std::move(ev));  // the timing graph records its own events
+    size_t i = 0;
+    for (; i < P.steps.size() && P.steps[i].varies; ++i) {
+      const cudaError_t err = P.steps[i].run(s);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        P.last_error = P.steps[i].name + ": " + cudaGetErrorString(err);
+        return HSVD_ECUDA;
+      }
+    }
+    const cudaError_t err = cudaGraphLaunch(P.tgraph_exec, s);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      P.last_error = std::string("graph launch: ") + cudaGetErrorString(err);
+      return HSVD_ECUDA;
+    }
+    P.pending.push_back(P.tev);
+    P.pending_rec.push_back(P.trec);
+    P.pending_owned.push_back(0);
+    P.ran = true;
+    P.last_stream = s;
+    return HSVD_OK;
+  }
   for (size_t i = 0; i < P.steps.size(); ++i) {
     const bool mark = timed && (all_steps || P.steps[i].kind == 5);
     if (mark && !rec[i]) {
@@ -1617,6 +1694,7 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
   if (timed) {
     P.pending.push_back(std::move(ev));
     P.pending_rec.push_back(std::move(rec));
+    P.pending_owned.push_back(1);
   }
   if (trace) {
     // Per-step device time of this run, summed by step name without the

@@ -380,3 +380,31 @@ def test_refine_stopping_rule_and_error_drop():
     assert before > 1e-4 and after < 0.8 * before, (before, after)
     plan.run([xd])
     assert plan.refine(4, 0.0)[0] == 4
+
+
+# ---------------------------------------------------------------- graph replay and timing modes
+
+def test_graph_replay_equals_step_launches_and_timing_modes():
+    """Untimed runs replay a CUDA graph of the launch list; timed runs launch
+    step by step (mode 1) or through a graph with events around the core
+    SVDs (mode 2).  The kernels and their order are the same, so the factors
+    are bitwise identical; mode 2 reports only the core-SVD steps."""
+    x = W.exp_decay(1024, 768, r=200, noise=1e-5, tag=111, dtype=np.float32)
+    xd = torch.from_numpy(x).cuda()
+    plan = hsvd.Plan(1024, 768, 256, 256, "fixed_k", 24, prec="bf16_mixed", power_iters=1)
+    outs = []
+    for mode in (0, 1, 2, 0):
+        plan.set_timing(mode)
+        plan.run([xd])
+        outs.append(plan.factors(0))
+        t, runs = plan.step_times()
+        kinds = [s["kind"] for s in plan.steps()]
+        if mode == 1:
+            assert runs == 1 and all(v > 0 for v in t)
+        if mode == 2:
+            assert runs == 1
+            bad = [(i, k, v) for i, (v, k) in enumerate(zip(t, kinds)) if (v > 0) != (k == "jacobi")]
+            assert not bad, bad
+    plan.set_timing(0)
+    for u, s, v in outs[1:]:
+        assert np.array_equal(u, outs[0][0]) and np.array_equal(s, outs[0][1]) and np.array_equal(v, outs[0][2])
