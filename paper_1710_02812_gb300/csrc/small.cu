@@ -1319,6 +1319,77 @@ __device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], 
   return true;
 }
 
+// The same rotation with the squared column norms a = |x|^2, b = |y|^2
+// carried along instead of recomputed: only c = x.y is reduced, and after a
+// rotation by t the norms are a - t c and b + t c (exact in exact arithmetic).
+// A norm that falls below a quarter of its value is recomputed from the
+// rotated column (the update would cancel); all norms are recomputed at the
+// start of every sweep, so rounding does not accumulate past one sweep.
+template <int RMAX>
+__device__ __forceinline__ bool bp_rotate_nt(float (&xr)[RMAX], float (&yr)[RMAX], float& a, float& b, float tol2,
+                                             float big2, int& big, float& cs, float& sn, unsigned gm) {
+  uint64_t c2[2] = {0, 0};
+#pragma unroll
+  for (int t = 0; t < RMAX / 2; ++t)
+    c2[t & 1] = f2_fma(f2_pack(xr[2 * t], xr[2 * t + 1]), f2_pack(yr[2 * t], yr[2 * t + 1]), c2[t & 1]);
+  float lo, hi;
+  f2_unpack(f2_add(c2[0], c2[1]), lo, hi);
+  float c = lo + hi;
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  const float ab = a * b, cc = c * c;
+  if (!(ab > 0.f && cc > tol2 * ab)) return false;
+  big |= cc > big2 * ab;
+  const float zeta = (b - a) * fast_rcp(2.f * c);
+  const float az = fabsf(zeta);
+  float t;
+  if (az < 1e18f) {
+    const float q1 = 1.f + az * az;
+    t = fast_rcp(az + q1 * rsq(q1));
+  } else {
+    t = 0.5f * fast_rcp(az);
+  }
+  if (zeta < 0.f) t = -t;
+  cs = rsq(1.f + t * t);
+  sn = cs * t;
+  const uint64_t cs2 = f2_pack(cs, cs), sn2 = f2_pack(sn, sn), nsn2 = f2_pack(-sn, -sn);
+#pragma unroll
+  for (int u = 0; u < RMAX / 2; ++u) {
+    const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]), y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
+    f2_unpack(f2_fma(cs2, x2, f2_mul(nsn2, y2)), xr[2 * u], xr[2 * u + 1]);
+    f2_unpack(f2_fma(sn2, x2, f2_mul(cs2, y2)), yr[2 * u], yr[2 * u + 1]);
+  }
+  const float tc = t * c;
+  float an = a - tc, bn = b + tc;
+  if (!(an >= 0.25f * a)) {  // group-uniform: a, t, c are the same in the group's lanes
+    uint64_t s2[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < RMAX / 2; ++u) {
+      const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]);
+      s2[u & 1] = f2_fma(x2, x2, s2[u & 1]);
+    }
+    f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
+    an = lo + hi;
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) an += __shfl_xor_sync(gm, an, off);
+  }
+  if (!(bn >= 0.25f * b)) {
+    uint64_t s2[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < RMAX / 2; ++u) {
+      const uint64_t y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
+      s2[u & 1] = f2_fma(y2, y2, s2[u & 1]);
+    }
+    f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
+    bn = lo + hi;
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) bn += __shfl_xor_sync(gm, bn, off);
+  }
+  a = an;
+  b = bn;
+  return true;
+}
+
 template <int RMAX>
 __device__ __forceinline__ void bp_load(const float* Mw, int col, int ldm, int lane, float (&r)[RMAX]) {
   const float4* p4 = reinterpret_cast<const float4*>(Mw + col * ldm) + lane;
@@ -1357,8 +1428,8 @@ __device__ __forceinline__ void bp_rotate_v(float* Vw, int ldv, int p, int q, in
 // rotated once per sweep, as in the cyclic ordering; shared memory is read and
 // written once per block round instead of once per round, and the CTA
 // barrier is taken once per block round.
-template <bool WANT_V, int RMAX, bool F2>
-__global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* __restrict__ tasks, int nccap,
+template <bool WANT_V, int RMAX, bool F2, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) k_jacobi_bp(const JacobiTask<float>* __restrict__ tasks, int nccap,
                                                       TruncParams tp, DevStatus* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* __restrict__ Mw = reinterpret_cast<float*>(smem_raw);
@@ -1366,6 +1437,7 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
   __shared__ int perm[512];
   __shared__ int rank_s;
   __shared__ float hh_scratch[520];
+  __shared__ float nrm[128];  // squared column norms carried through a sweep (F2 path)
   constexpr int G = 8;
   constexpr int rows_pad = G * RMAX;
   const JacobiTask<float>& tk = tasks[blockIdx.x];
@@ -1426,8 +1498,28 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
   const float big2 = static_cast<float>(told);
   bool converged = (nc <= 1);
   int sweep = 0;
+  const unsigned gm8 = 0xffu << ((tid & 31) & ~7);
   for (; sweep < tp.max_sweeps && !converged; ++sweep) {
     int big = 0;
+    if constexpr (F2) {  // exact squared norms at the start of the sweep
+      for (int j = tid >> 3; j < n8; j += nt >> 3) {  // uniform per warp: n8, nt / 8 multiples of 4
+        float xr[RMAX];
+        bp_load<RMAX>(Mw, j, ldm, lane, xr);
+        uint64_t s2[2] = {0, 0};
+#pragma unroll
+        for (int u = 0; u < RMAX / 2; ++u) {
+          const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]);
+          s2[u & 1] = f2_fma(x2, x2, s2[u & 1]);
+        }
+        float lo, hi;
+        f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
+        float a = lo + hi;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) a += __shfl_xor_sync(gm8, a, off);
+        if (lane == 0) nrm[j] = a;
+      }
+      __syncthreads();
+    }
     // pairs inside each block: warp w holds blocks 2w (groups 0, 1) and 2w + 1
     {
       const int blk = 2 * warp + (grp >> 1), h = grp & 1;
@@ -1447,7 +1539,17 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
           for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
         }
         float cs = 1.f, sn = 0.f;
-        const bool rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+        bool rot;
+        if constexpr (F2) {
+          float a = act ? nrm[p] : 0.f, b = act ? nrm[q] : 0.f;
+          rot = bp_rotate_nt<RMAX>(xr, yr, a, b, tol2, big2, big, cs, sn, gm8);
+          if (act && rot && lane == 0) {
+            nrm[p] = a;
+            nrm[q] = b;
+          }
+        } else {
+          rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+        }
         if (act && rot) {
           bp_store<RMAX>(Mw, p, ldm, lane, xr);
           bp_store<RMAX>(Mw, q, ldm, lane, yr);
@@ -1462,10 +1564,15 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
     for (int R = 0; R < nb - 1; ++R) {
       int I = 0, J = 0;
       float xr[RMAX], yr[RMAX];
+      float na = 0.f, nbb = 0.f;  // carried squared norms of the group's x and y columns (F2 path)
       if (wact) {
         rr_pair(nb, R, warp, I, J);
         bp_load<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
         bp_load<RMAX>(Mw, 4 * J + grp, ldm, lane, yr);
+        if constexpr (F2) {
+          na = nrm[4 * I + grp];
+          nbb = nrm[4 * J + grp];
+        }
       } else {
 #pragma unroll
         for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
@@ -1473,7 +1580,11 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
 #pragma unroll 1
       for (int t = 0; t < 4; ++t) {
         float cs = 1.f, sn = 0.f;
-        const bool rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+        bool rot;
+        if constexpr (F2)
+          rot = bp_rotate_nt<RMAX>(xr, yr, na, nbb, tol2, big2, big, cs, sn, gm8);
+        else
+          rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
         if (WANT_V) {
           if (wact && rot) bp_rotate_v(Vw, ldv, 4 * I + grp, 4 * J + ((grp + t) & 3), nc, lane, cs, sn);
           __syncwarp();
@@ -1481,11 +1592,16 @@ __global__ void __launch_bounds__(512, 1) k_jacobi_bp(const JacobiTask<float>* _
         if (t < 3) {
 #pragma unroll
           for (int u = 0; u < RMAX; ++u) yr[u] = __shfl_sync(0xffffffffu, yr[u], (tid + 8) & 31);
+          if constexpr (F2) nbb = __shfl_sync(0xffffffffu, nbb, (tid + 8) & 31);
         }
       }
       if (wact) {
         bp_store<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
         bp_store<RMAX>(Mw, 4 * J + ((grp + 3) & 3), ldm, lane, yr);
+        if (F2 && lane == 0) {
+          nrm[4 * I + grp] = na;
+          nrm[4 * J + ((grp + 3) & 3)] = nbb;
+        }
       }
       __syncthreads();
     }
@@ -1657,6 +1773,19 @@ static cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, 
     const char* e = std::getenv("HSVD_JACOBI_F2");
     return !(e && e[0] == '0');
   }();
+  // more cores than SMs: two CTAs per SM (64 registers a thread) so a level
+  // of 256 cores runs in one wave
+  static const int nsm = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return v > 0 ? v : 152;
+  }();
+  if (f2 && !want_v && rmax == 16 && ntasks > nsm && 2 * (bytes + 8 * 1024) <= 220 * 1024)
+    return go(k_jacobi_bp<false, 16, true, 2>);
   if (f2) {
     switch (rmax * 2 + (want_v ? 1 : 0)) {
       case 8: return go(k_jacobi_bp<false, 4, true>);
