@@ -408,3 +408,22 @@ def test_graph_replay_equals_step_launches_and_timing_modes():
     plan.set_timing(0)
     for u, s, v in outs[1:]:
         assert np.array_equal(u, outs[0][0]) and np.array_equal(s, outs[0][1]) and np.array_equal(v, outs[0][2])
+
+
+# ---------------------------------------------------------------- tall-skinny blocks, gamma rule (the paper's sweeps)
+
+@pytest.mark.parametrize("bc", [8, 16, 64])
+@pytest.mark.parametrize("prec", ["f32", "bf16_mixed"])
+def test_gamma_tall_skinny_blocks(bc, prec):
+    """The paper's experiments cut CFD snapshot matrices (m x 1024, m ~ 1e5)
+    into tall blocks only 8-64 columns wide and truncate with gamma = 1e-2
+    (Section 4).  A quarter-size stand-in (33025 x 256, a ragged last slab)
+    with a decaying spectrum that leaves ~28 modes above gamma: many narrow
+    blocks, many small merges."""
+    s_true = np.exp(-np.arange(60) / 6.0)
+    x = W.planted(33025, 256, s_true, noise=1e-6, tag=120 + bc).astype(np.float32)
+    xin = W.bf16_round(x) if prec == "bf16_mixed" else x
+    (got,), st, _ = run_gpu([xin], 8192, bc, "gamma", 1e-2, prec, rank_cap=64, power_iters=2)
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0
+    ref = oracle_run(xin, 8192, bc, "gamma", 1e-2, prec, rank_cap=64)
+    check(xin, got, ref, prec, f"gamma {bc}-wide {prec}", s_true=s_true)
