@@ -145,8 +145,12 @@ hsvd_status hsvd_run(hsvd_plan_t plan, const void* const* A, const int64_t* lda,
 
 /* hsvd_run_host -- as hsvd_run, but A[i] are HOST pointers: the matrices
  * are copied to plan-owned device staging on `stream` first (the plan must
- * have been made with opts->host_staging != 0, else EINVAL).  Host memory
- * must stay valid until the stream has passed the copies. */
+ * have been made with opts->host_staging != 0, else EINVAL).  On the
+ * BF16-mixed path, page-locked host memory that the device can address is
+ * not copied: the conversion kernel reads it in place (over NVLink-C2C on
+ * Grace systems) while it writes the BF16 copies.  Host memory must stay
+ * valid until the stream has passed the copies (or that kernel), and
+ * unchanged until hsvd_refine is done with it. */
 hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream);
 
 /* hsvd_refine -- Alg. 2 (iterative improvement) on the factors of the last

@@ -127,6 +127,8 @@ struct PlanImpl {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  void* fscratch = nullptr;  // column-major staging of factors copied to the host
+  size_t fscratch_bytes = 0;
   // timing mode 2 with graphs: a second graph with event-record nodes around
   // the core-SVD steps; its events hold the last replay's times
   cudaGraph_t tgraph = nullptr;
@@ -144,6 +146,7 @@ struct PlanImpl {
     for (auto e : tev)
       if (e) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (fscratch) cudaFree(fscratch);
     if (arena) cudaFree(arena);
     if (tables) cudaFree(tables);
     if (d_mats) cudaFree(d_mats);
@@ -1750,9 +1753,26 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
   std::vector<const void*> dptr(P.batch);
   std::vector<int64_t> dld(P.batch);
   for (int b = 0; b < P.batch; ++b) {
+    // The BF16-mixed path reads its input once, in the conversion step: when
+    // the device can address the host buffer (page-locked memory, reached over
+    // NVLink-C2C on Grace systems) that step reads it in place, and the
+    // transfer overlaps the conversion instead of preceding it.
+    if (P.mixed) {
+      cudaPointerAttributes attr;
+      if (cudaPointerGetAttributes(&attr, A[b]) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+          attr.devicePointer) {
+        dptr[b] = attr.devicePointer;
+        dld[b] = lda[b];
+        continue;
+      }
+      cudaGetLastError();
+    }
     const size_t w = (size_t)P.n[b] * P.in_elem;
-    const cudaError_t e = cudaMemcpy2DAsync(P.staging[b], w, A[b], (size_t)lda[b] * P.in_elem, w,
-                                            (size_t)P.m[b], cudaMemcpyHostToDevice, s);
+    const cudaError_t e =
+        lda[b] == P.n[b]
+            ? cudaMemcpyAsync(P.staging[b], A[b], w * (size_t)P.m[b], cudaMemcpyHostToDevice, s)
+            : cudaMemcpy2DAsync(P.staging[b], w, A[b], (size_t)lda[b] * P.in_elem, w, (size_t)P.m[b],
+                                cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       P.last_error = std::string("host-to-device copy: ") + cudaGetErrorString(e);
@@ -1868,32 +1888,51 @@ hsvd_status hsvd_factors(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* U, 
     }
     return HSVD_OK;
   }
+  // Host destination: the layout change runs on the device into plan-owned
+  // scratch, then one copy per factor (no per-element host work).
+  const size_t need = (size_t)(mo + no) * kc * el;
+  if (P.fscratch_bytes < need) {
+    if (P.fscratch) cudaFree(P.fscratch);
+    P.fscratch = nullptr;
+    P.fscratch_bytes = 0;
+    if (cudaMalloc(&P.fscratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return HSVD_ENOMEM;
+    }
+    P.fscratch_bytes = need;
+  }
+  char* du = static_cast<char*>(P.fscratch);
+  char* dv = du + (size_t)mo * kc * el;
   int rk = 0;
-  std::vector<char> hu, hv;
-  cudaError_t e = cudaMemcpyAsync(&rk, po.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && U) {
-    hu.resize((size_t)mo * kc * el);
-    e = cudaMemcpyAsync(hu.data(), su, hu.size(), cudaMemcpyDeviceToHost, s);
-  }
-  if (e == cudaSuccess && V) {
-    hv.resize((size_t)no * kc * el);
-    e = cudaMemcpyAsync(hv.data(), sv, hv.size(), cudaMemcpyDeviceToHost, s);
-  }
+  cudaError_t e = cudaSuccess;
+  if (U)
+    e = (el == 8) ? hsvd::launch_rowmajor_to_colmajor<double>(static_cast<double*>(su), kc, (int)mo, po.rank, kc,
+                                                              reinterpret_cast<double*>(du), mo, s)
+                  : hsvd::launch_rowmajor_to_colmajor<float>(static_cast<float*>(su), kc, (int)mo, po.rank, kc,
+                                                             reinterpret_cast<float*>(du), mo, s);
+  if (e == cudaSuccess && V)
+    e = (el == 8) ? hsvd::launch_rowmajor_to_colmajor<double>(static_cast<double*>(sv), kc, (int)no, po.rank, kc,
+                                                              reinterpret_cast<double*>(dv), no, s)
+                  : hsvd::launch_rowmajor_to_colmajor<float>(static_cast<float*>(sv), kc, (int)no, po.rank, kc,
+                                                             reinterpret_cast<float*>(dv), no, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rk, po.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  rk = std::max(0, std::min(rk, kc));
+  if (e == cudaSuccess && U && rk > 0)
+    e = ldu == mo ? cudaMemcpyAsync(U, du, (size_t)mo * rk * el, cudaMemcpyDeviceToHost, s)
+                  : cudaMemcpy2DAsync(U, (size_t)ldu * el, du, (size_t)mo * el, (size_t)mo * el, rk,
+                                      cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && V && rk > 0)
+    e = ldv == no ? cudaMemcpyAsync(V, dv, (size_t)no * rk * el, cudaMemcpyDeviceToHost, s)
+                  : cudaMemcpy2DAsync(V, (size_t)ldv * el, dv, (size_t)no * el, (size_t)no * el, rk,
+                                      cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, po.sig, el * kc, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return HSVD_ECUDA;
   }
-  rk = std::max(0, std::min(rk, kc));
   if (rank) *rank = rk;
-  auto transpose = [&](const std::vector<char>& src, int64_t rows, void* dst, int64_t ldd) {
-    for (int c = 0; c < rk; ++c)
-      for (int64_t i = 0; i < rows; ++i)
-        std::memcpy(static_cast<char*>(dst) + (c * ldd + i) * el, src.data() + (i * kc + c) * el, el);
-  };
-  if (U) transpose(hu, mo, U, ldu);
-  if (V) transpose(hv, no, V, ldv);
   return HSVD_OK;
 }
 
@@ -1903,6 +1942,7 @@ int64_t hsvd_workspace_bytes(hsvd_plan_t plan) {
   int64_t t = (int64_t)P.arena_bytes + (int64_t)P.tables_bytes;
   if (P.d_tmaps) t += (int64_t)P.tmaps.size() * 128;
   for (size_t b = 0; b < P.staging.size(); ++b) t += P.m[b] * P.n[b] * (int64_t)P.in_elem;
+  t += (int64_t)P.fscratch_bytes;
   return t;
 }
 
