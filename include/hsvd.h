@@ -177,6 +177,18 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
 hsvd_status hsvd_refine(hsvd_plan_t plan, int32_t max_iters, double eps, int32_t* iters, double* error,
                         void* stream);
 
+/* hsvd_gram -- G = X^T X for a device matrix X (m x n, row-major, leading
+ * dimension ldx >= n) into device G (n x n, row-major, ldg >= n): the input
+ * of the paper's X^T X experiment (Section 4), which runs the method on the
+ * Gram matrix of a tall snapshot matrix.  prec HSVD_PREC_F32 (float X and G)
+ * or HSVD_PREC_F64 (double); other values EUNSUPPORTED.  Asynchronous on
+ * `stream`; its temporary tables and split-K partials are stream-ordered
+ * allocations released on the same stream.  The sum over rows is split into
+ * chunks added in a fixed order, so the result is deterministic.
+ * EINVAL: NULL pointers, m or n < 1, ld too small.  ENOMEM, ECUDA. */
+hsvd_status hsvd_gram(const void* X, int64_t ldx, int64_t m, int64_t n, hsvd_prec prec, void* G, int64_t ldg,
+                      void* stream);
+
 /* hsvd_status_query -- read the device status words of the last run.
  * sync != 0 synchronises the plan's last stream first; with sync == 0 the
  * values may be stale.  `r` must not be NULL. */

@@ -721,9 +721,10 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
   if (kcap > 256) return cudaErrorInvalidValue;
   {
     const int kb = kcap <= 32 ? 2 : kcap <= 64 ? 4 : kcap <= 128 ? 8 : 16;
-    if (kb <= 8) {
-      // shared memory only for staging R2 and R1 of the CholeskyQR2 product
-      const size_t rb = with_product ? 2 * (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T) : 0;
+    // shared memory only for staging R2 and R1 of the CholeskyQR2 product
+    // (FP64 at 128 x 128 needs 264 KB: that case takes the tiled kernel)
+    const size_t rb = with_product ? 2 * (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T) : 0;
+    if (kb <= 8 && rb <= 200 * 1024) {
       auto go = [&](auto kern) -> cudaError_t {
         if (rb > 48 * 1024) {
           cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);

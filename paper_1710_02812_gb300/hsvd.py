@@ -27,7 +27,7 @@ EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
             "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error",
-            "hsvd_refine")
+            "hsvd_refine", "hsvd_gram")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -106,6 +106,8 @@ def lib():
         L.hsvd_last_error.restype = ctypes.c_char_p
         L.hsvd_refine.argtypes = [P, i32, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), P]
         L.hsvd_refine.restype = ctypes.c_int
+        L.hsvd_gram.argtypes = [P, i64, i64, i64, ctypes.c_int, P, i64, P]
+        L.hsvd_gram.restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -173,6 +175,20 @@ def hsvd_refine(plan, max_iters: int, eps: float, stream=None):
     if code != HSVD_OK:
         raise HsvdError(code, "hsvd_refine" + _detail(plan))
     return it.value, err.value
+
+
+def hsvd_gram(X, G, stream=None):
+    """G = X^T X on the device (torch tensors: X m x n, G n x n, both float32 or
+    both float64, row-major with unit column stride)."""
+    import torch
+    if X.dtype != G.dtype or X.dtype not in (torch.float32, torch.float64):
+        raise TypeError("X and G must both be float32 or both float64")
+    if X.stride(1) != 1 or G.stride(1) != 1:
+        raise ValueError("rows must be contiguous")
+    m, n = X.shape
+    prec = PREC["f64"] if X.dtype == torch.float64 else PREC["f32"]
+    _check(lib().hsvd_gram(X.data_ptr(), X.stride(0), m, n, prec, G.data_ptr(), G.stride(0), _stream_ptr(stream)),
+           "hsvd_gram")
 
 
 def hsvd_last_error(plan) -> str:

@@ -112,6 +112,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.hsvd_launches_per_run(None) == -1
     assert lib.hsvd_last_error(None) == b""
     assert lib.hsvd_refine(None, 1, 1e-3, None, None, None) == hsvd.HSVD_EINVAL
+    assert lib.hsvd_gram(None, 4, 4, 4, 1, None, 4, None) == hsvd.HSVD_EINVAL
     lib.hsvd_destroy(None)
 
 

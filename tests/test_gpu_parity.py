@@ -427,3 +427,34 @@ def test_gamma_tall_skinny_blocks(bc, prec):
     assert st["not_converged"] == 0 and st["nonfinite"] == 0
     ref = oracle_run(xin, 8192, bc, "gamma", 1e-2, prec, rank_cap=64)
     check(xin, got, ref, prec, f"gamma {bc}-wide {prec}", s_true=s_true)
+
+
+# ---------------------------------------------------------------- the X^T X variant (Section 4)
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gram_variant(prec):
+    """Section 4 also runs the method on X^T X of a tall snapshot matrix.
+    hsvd_gram forms X^T X on the device (checked against the FP64 product);
+    the method on it matches the oracle on the same Gram bytes, and its
+    singular values are the squares of X's (top gap-separated modes)."""
+    s_true = np.exp(-np.arange(80) / 8.0)
+    x = W.planted(20000, 384, s_true, noise=1e-6, tag=140)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    xd = torch.from_numpy(x).to(dt).cuda()
+    g = torch.empty((384, 384), dtype=dt, device="cuda")
+    hsvd.hsvd_gram(xd, g)
+    torch.cuda.synchronize()
+    gh = g.cpu().numpy()
+    xr = xd.cpu().numpy().astype(np.float64)
+    exact = xr.T @ xr
+    err = np.abs(gh - exact).max() / np.abs(exact).max()
+    assert err <= (1e-14 if prec == "f64" else 2e-6), err
+    # the paper's gamma = 1e-4 on X^T X (~1e-2 on X); FP32 cannot resolve
+    # sigma ~ 1e-4 sigma_1 to 1e-4 relative, so its run keeps gamma = 1e-2
+    gamma = 1e-4 if prec == "f64" else 1e-2
+    (got,), st, _ = run_gpu([gh], 128, 64, "gamma", gamma, prec, rank_cap=64, power_iters=2)
+    ref = oracle_run(gh, 128, 64, "gamma", gamma, prec, rank_cap=64)
+    check(gh, got, ref, prec, f"gram {prec}", s_true=s_true ** 2)
+    s_x = np.linalg.svd(xr, compute_uv=False)
+    lead = 10  # sigma(G) >= 0.08 sigma_1: far above every truncation of the method
+    assert np.allclose(got[1][:lead], s_x[:lead] ** 2, rtol=1e-6 if prec == "f64" else 1e-4, atol=0)
