@@ -726,7 +726,7 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
     const size_t rb = with_product ? 2 * (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T) : 0;
     if (kb <= 8 && rb <= 200 * 1024) {
       auto go = [&](auto kern) -> cudaError_t {
-        if (rb > 48 * 1024) {
+        if (rb > 16 * 1024) {  // the kernels also hold static shared memory
           cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb);
           if (e != cudaSuccess) return e;
         }
@@ -740,7 +740,7 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
     const size_t tb = (size_t)(16 * kb) * (16 * kb + 1) * sizeof(T);
     if (tb <= 200 * 1024) {
       auto go = [&](auto kern) -> cudaError_t {
-        if (tb > 48 * 1024) {
+        if (tb > 16 * 1024) {  // the kernels also hold static shared memory
           cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
           if (e != cudaSuccess) return e;
         }
@@ -755,7 +755,7 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
   }
   const size_t bytes = (size_t)kcap * kcap * sizeof(T);
   if (bytes <= 200 * 1024) {
-    if (bytes > 48 * 1024) {
+    if (bytes > 16 * 1024) {  // the kernels also hold static shared memory
       cudaError_t e =
           cudaFuncSetAttribute(k_chol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
@@ -1651,7 +1651,7 @@ static cudaError_t launch_jacobi_v(const JacobiTask<T>* tasks, int ntasks, int n
   const int use_smem = bytes <= 200 * 1024;
   const size_t dyn = use_smem ? bytes : 0;
   auto go = [&](auto kern) -> cudaError_t {
-    if (dyn > 48 * 1024) {
+    if (dyn > 16 * 1024) {  // the kernels also hold static shared memory
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       if (e != cudaSuccess) return e;
     }
@@ -1713,7 +1713,7 @@ static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int 
   const int tmax = rmax >= 16 ? 512 : 1024;  // the kernel's launch bound
   threads = threads < 32 ? 32 : (threads > tmax ? tmax : ((threads + 31) / 32) * 32);
   auto go = [&](auto kern) -> cudaError_t {
-    if (bytes > 48 * 1024) {
+    if (bytes > 16 * 1024) {  // the kernels also hold static shared memory
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
     }
@@ -1761,7 +1761,7 @@ static cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, 
   if (bytes > 200 * 1024) return cudaSuccess;
   const int threads = ((nccap + 7) & ~7) * 4;  // one warp per block pair
   auto go = [&](auto kern) -> cudaError_t {
-    if (bytes > 48 * 1024) {
+    if (bytes > 16 * 1024) {  // the kernels also hold static shared memory
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
     }
