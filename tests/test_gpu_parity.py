@@ -502,3 +502,41 @@ def test_seeded_shape_sweep(i, m, n, br, bc, k, prec, tree):
     # above that level are determined
     s_gate = s_true if prec != "bf16_mixed" else s_true[s_true >= 0.05 * s_true[0]]
     check(xin, got, ref, prec, f"sweep {i} {m}x{n}/{br}x{bc} k={k} r={r} {prec} {tree}", s_true=s_gate)
+
+
+def _sweep_rule_cases():
+    g = np.random.default_rng(20260103)
+    cases = []
+    for i in range(9):
+        mode = ["gamma", "energy"][i % 2]
+        prec = ["f32", "bf16_mixed", "f64"][i % 3]
+        sizes = [(int(g.integers(64, 700)), int(g.integers(64, 700))) for _ in range(1 + i % 3)]
+        br, bc = int(g.integers(32, 300)), int(g.integers(32, 300))
+        if prec == "bf16_mixed" and i % 2:
+            br, bc = br // 8 * 8, bc // 8 * 8
+        cases.append((i, mode, prec, sizes, br, bc))
+    return cases
+
+
+@pytest.mark.parametrize("i,mode,prec,sizes,br,bc", _sweep_rule_cases())
+def test_seeded_rule_and_batch_sweep(i, mode, prec, sizes, br, bc):
+    """Gamma and energy rules on batches of 1-3 uneven matrices (seeded): a
+    planted spectrum with a factor-1000 drop after r1 values plus 1e-6 noise,
+    so each rule's decision is far from its threshold and unique."""
+    g = np.random.default_rng(3000 + i)
+    xs, trues = [], []
+    for j, (m, n) in enumerate(sizes):
+        r1 = int(g.integers(2, 12))
+        top = np.sort(g.uniform(0.5, 2.0, r1))[::-1] * (0.85 ** np.arange(r1))
+        s_true = np.concatenate([top, 1e-3 * top[-1] * 0.5 ** np.arange(6)])
+        x = W.planted(m, n, s_true, noise=1e-6, tag=4000 + 10 * i + j)
+        if prec == "bf16_mixed":
+            x = W.bf16_round(x.astype(np.float32))
+        xs.append(x if prec == "f64" else np.asarray(x, np.float32))
+        trues.append(top)
+    param = 1e-2 if mode == "gamma" else 0.999
+    outs, st, _ = run_gpu(xs, br, bc, mode, param, prec, rank_cap=32, power_iters=4)
+    assert st["nonfinite"] == 0
+    for x, got, top in zip(xs, outs, trues):
+        ref = oracle_run(x, br, bc, mode, param, prec, rank_cap=32)
+        check(x, got, ref, prec, f"rules {i} {mode} {prec} {x.shape}/{br}x{bc}", s_true=top)
