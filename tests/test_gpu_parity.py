@@ -540,3 +540,27 @@ def test_seeded_rule_and_batch_sweep(i, mode, prec, sizes, br, bc):
     for x, got, top in zip(xs, outs, trues):
         ref = oracle_run(x, br, bc, mode, param, prec, rank_cap=32)
         check(x, got, ref, prec, f"rules {i} {mode} {prec} {x.shape}/{br}x{bc}", s_true=top)
+
+
+# ---------------------------------------------------------------- limits of the planner
+
+@pytest.mark.parametrize("m,n,br,bc,k,prec", [
+    (640, 512, 320, 256, 100, "f64"),          # 200-wide FP64 sketches and cores (global-memory kernels)
+    (1024, 1024, 512, 512, 128, "bf16_mixed"),  # 256-wide tensor-core operands, 256 x 256 cores on clusters
+    (1, 300, 1, 64, 1, "f32"),                  # one row
+    (300, 1, 64, 1, 1, "f32"),                  # one column
+    (5, 7, 2, 3, 2, "f32"),                     # 3 x 3 grid of 2 x 3 blocks, ragged
+    (50, 40, 64, 64, 60, "f32"),                # k above min(m, n), one partial block
+])
+def test_planner_limits(m, n, br, bc, k, prec):
+    r = min(m, n, 20)
+    s_true = 0.8 ** np.arange(r)
+    x = W.planted(m, n, s_true, noise=0.0, tag=5000 + m + n)
+    if prec == "bf16_mixed":
+        x = W.bf16_round(x.astype(np.float32))
+    xin = x if prec == "f64" else np.asarray(x, np.float32)
+    (got,), st, _ = run_gpu([xin], br, bc, "fixed_k", k, prec, power_iters=4)
+    assert st["nonfinite"] == 0 and st["not_converged"] == 0
+    ref = oracle_run(xin, br, bc, "fixed_k", k, prec)
+    gate = s_true if prec != "bf16_mixed" else s_true[s_true >= 0.05]
+    check(xin, got, ref, prec, f"limits {m}x{n}/{br}x{bc} k={k} {prec}", s_true=gate)
