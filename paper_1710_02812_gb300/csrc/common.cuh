@@ -148,6 +148,16 @@ cudaError_t launch_gemm_nn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* it
 template <class TA, class TB, class TC>
 cudaError_t launch_gemm_tn(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                            const MatRef* mats, cudaStream_t s);
+// FP32 products with at most 32 output rows and columns (TN) or at most 32
+// inner rows and output columns (NN); same items and partials as k_gemm2.
+constexpr int GEMM_SKINNY = 32;
+// sk: the launch's largest dimension among those bounded (8, 16 or 32 kernels)
+template <class TA>
+cudaError_t launch_gemm_tn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
+                                  int sk, const MatRef* mats, cudaStream_t s);
+template <class TA>
+cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
+                                  int sk, const MatRef* mats, cudaStream_t s);
 template <class TA, class TB, class TC>
 cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem* items, int nitems,
                                cudaStream_t s);

@@ -451,6 +451,147 @@ __global__ void __launch_bounds__(256) k_gemm2_reduce(const GemmTask<TA, float, 
   }
 }
 
+// ---------------------------------------------------------------- skinny (FP32)
+// Products with at most 32 output columns and (NN) at most 32 inner rows or
+// (TN) at most 32 output rows: the 128 x 64 tile of k_gemm2 would be mostly
+// padding (narrow blocks and low-rank merges), so these kernels size the work
+// to the product.  Items and split-K partials keep k_gemm2's layout (one
+// 128 x 64 tile per task), so the same reduction kernel applies.
+constexpr int SK = 32;
+
+// TN: C (M x N) = A^T B over a K chunk; A: K x M, B: K x N (row-major),
+// M, N <= SK.  64-row slabs of A and B staged in shared memory; the SK x SK
+// outputs are spread over the 256 threads (several per thread for SK = 32;
+// for SK = 8 four thread groups split the rows and add up at the end).
+template <class TA, int SK>
+__global__ void __launch_bounds__(256) k_gemm_tn_skinny(const GemmTask<TA, float, float>* __restrict__ tasks,
+                                                        const GemmItem* __restrict__ items,
+                                                        const MatRef* __restrict__ mats) {
+  constexpr int NO = SK * SK;
+  constexpr int OPT = NO > 256 ? NO / 256 : 1;     // outputs per thread
+  constexpr int GROUPS = NO < 256 ? 256 / NO : 1;  // thread groups splitting the rows
+  __shared__ float As[64][SK + 1];
+  __shared__ float Bs[64][SK + 1];
+  __shared__ float red[GROUPS > 1 ? GROUPS * NO : 1];
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask<TA, float, float>& tk = tasks[it.task];
+  const int M = eff(tk.M), N = eff(tk.N), K = eff(tk.K);
+  int kb = 0, ke = K;
+  if (tk.kchunk > 0) {
+    kb = it.kc * tk.kchunk;
+    ke = min(K, kb + tk.kchunk);
+  }
+  const TA* A = tk.A;
+  int64_t lda = tk.lda;
+  if (tk.mat >= 0) {
+    const MatRef mr = mats[tk.mat];
+    A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+    lda = mr.ld;
+  }
+  const int t = threadIdx.x;
+  const int g = t / (NO < 256 ? NO : 256), tl = t % (NO < 256 ? NO : 256);
+  float acc[OPT];
+#pragma unroll
+  for (int q = 0; q < OPT; ++q) acc[q] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += 64) {
+    for (int e = t; e < 64 * SK; e += 256) {
+      const int r = e / SK, c = e % SK, gk = k0 + r;
+      As[r][c] = (gk < ke && c < M) ? static_cast<float>(A[(int64_t)gk * lda + c]) : 0.f;
+      Bs[r][c] = (gk < ke && c < N) ? tk.B[(int64_t)gk * tk.ldb + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = g; r < 64; r += GROUPS) {
+#pragma unroll
+      for (int q = 0; q < OPT; ++q) {
+        const int o = tl + 256 * q;
+        acc[q] = fmaf(As[r][o / SK], Bs[r][o % SK], acc[q]);
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (GROUPS > 1) {
+    red[g * NO + tl] = acc[0];
+    __syncthreads();
+    if (g != 0) return;
+    for (int h = 1; h < GROUPS; ++h) acc[0] += red[h * NO + tl];
+  }
+#pragma unroll
+  for (int q = 0; q < OPT; ++q) {
+    const int o = tl + 256 * q, i = o / SK, j = o % SK;
+    if (i >= M || j >= N) continue;
+    if (tk.partial) {
+      const int64_t tile_stride = (int64_t)tk.mtiles * tk.ntiles * (BM2 * BN2);
+      tk.partial[it.kc * tile_stride + i * BN2 + j] = acc[q];
+    } else {
+      float v = tk.alpha * acc[q];
+      if (tk.C0) v += tk.beta * tk.C0[(int64_t)i * tk.ldc0 + j];
+      tk.C[(int64_t)i * tk.ldc + j] = v;
+    }
+  }
+}
+
+// NN: C = [A | A2] B (+ beta C0) with K1 + K2 <= SK and N <= SK; one thread
+// per row of a 128-row tile, the tile's A rows and B staged in shared memory.
+template <class TA, int SK>
+__global__ void __launch_bounds__(128) k_gemm_nn_skinny(const GemmTask<TA, float, float>* __restrict__ tasks,
+                                                        const GemmItem* __restrict__ items,
+                                                        const MatRef* __restrict__ mats) {
+  __shared__ float As[128][SK + 1];
+  __shared__ float Bs[SK][SK + 1];
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask<TA, float, float>& tk = tasks[it.task];
+  const int M = eff(tk.M), N = eff(tk.N), K1 = eff(tk.K);
+  const int K2 = tk.A2 ? eff(tk.K2) : 0;
+  const int m0 = it.mt * 128;
+  if (m0 >= M) return;
+  const TA* A = tk.A;
+  int64_t lda = tk.lda;
+  if (tk.mat >= 0) {
+    const MatRef mr = mats[tk.mat];
+    A = static_cast<const TA*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+    lda = mr.ld;
+  }
+  const int t = threadIdx.x;
+  for (int e = t; e < SK * SK; e += 128) {
+    const int r = e / SK, c = e % SK;
+    Bs[r][c] = (r < K1 + K2 && c < N) ? tk.B[(int64_t)r * tk.ldb + c] : 0.f;
+  }
+  for (int e = t; e < 128 * SK; e += 128) {
+    const int r = e / SK, c = e % SK, gm = m0 + r;
+    float v = 0.f;
+    if (gm < M) {
+      if (c < K1)
+        v = static_cast<float>(A[(int64_t)gm * lda + c]);
+      else if (c < K1 + K2)
+        v = static_cast<float>(tk.A2[(int64_t)gm * tk.lda2 + (c - K1)]);
+    }
+    As[r][c] = v;
+  }
+  __syncthreads();
+  float acc[SK];
+#pragma unroll
+  for (int j = 0; j < SK; ++j) acc[j] = 0.f;
+  const int Kt = K1 + K2;
+  for (int k = 0; k < Kt; ++k) {
+    const float a = As[t][k];
+#pragma unroll
+    for (int j = 0; j < SK; ++j) acc[j] = fmaf(a, Bs[k][j], acc[j]);
+  }
+  __syncthreads();
+  // stage the results through shared memory so the row writes coalesce
+#pragma unroll
+  for (int j = 0; j < SK; ++j) As[t][j] = acc[j];
+  __syncthreads();
+  for (int e = t; e < 128 * SK; e += 128) {
+    const int r = e / SK, c = e % SK, gm = m0 + r;
+    if (gm >= M || c >= N) continue;
+    float v = tk.alpha * As[r][c];
+    if (tk.C0) v += tk.beta * tk.C0[(int64_t)gm * tk.ldc0 + c];
+    tk.C[(int64_t)gm * tk.ldc + c] = v;
+  }
+}
+
 }  // namespace
 
 template <class TA, class TB, class TC>
@@ -485,6 +626,39 @@ cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem
     k_gemm_reduce<TA, TB, TC><<<nitems, NT, 0, s>>>(tasks, items);
   return cudaGetLastError();
 }
+
+template <class TA>
+cudaError_t launch_gemm_tn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
+                                  int sk, const MatRef* mats, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (sk <= 8)
+    k_gemm_tn_skinny<TA, 8><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else if (sk <= 16)
+    k_gemm_tn_skinny<TA, 16><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else
+    k_gemm_tn_skinny<TA, 32><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  return cudaGetLastError();
+}
+template <class TA>
+cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
+                                  int sk, const MatRef* mats, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (sk <= 8)
+    k_gemm_nn_skinny<TA, 8><<<nitems, 128, 0, s>>>(tasks, items, mats);
+  else if (sk <= 16)
+    k_gemm_nn_skinny<TA, 16><<<nitems, 128, 0, s>>>(tasks, items, mats);
+  else
+    k_gemm_nn_skinny<TA, 32><<<nitems, 128, 0, s>>>(tasks, items, mats);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm_tn_skinny<float>(const GemmTask<float, float, float>*, const GemmItem*, int, int,
+                                                  const MatRef*, cudaStream_t);
+template cudaError_t launch_gemm_tn_skinny<__nv_bfloat16>(const GemmTask<__nv_bfloat16, float, float>*,
+                                                          const GemmItem*, int, int, const MatRef*, cudaStream_t);
+template cudaError_t launch_gemm_nn_skinny<float>(const GemmTask<float, float, float>*, const GemmItem*, int, int,
+                                                  const MatRef*, cudaStream_t);
+template cudaError_t launch_gemm_nn_skinny<__nv_bfloat16>(const GemmTask<__nv_bfloat16, float, float>*,
+                                                          const GemmItem*, int, int, const MatRef*, cudaStream_t);
 
 #define HSVD_INST(TA, TB, TC)                                                                              \
   template cudaError_t launch_gemm_nn<TA, TB, TC>(const GemmTask<TA, TB, TC>*, const GemmItem*, int,     \

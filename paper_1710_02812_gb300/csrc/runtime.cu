@@ -377,8 +377,21 @@ struct Builder {
     const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
     const int ni = (int)items.size();
     using TAx = typename TaOf<G>::type;
+    // narrow products (at most 32 output rows/columns for TN, 32 inner rows
+    // and output columns for NN) take the skinny FP32 kernels
+    bool skinny = std::is_same<T, float>::value;
+    int sk = 1;
+    for (const auto& g : tasks) {
+      const int kin = g.K.cap + (g.A2 ? g.K2.cap : 0);
+      sk = std::max(sk, std::max(is_tn ? g.M.cap : kin, g.N.cap));
+    }
+    if (sk > GEMM_SKINNY) skinny = false;
     if (is_tn) {
-      P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
+      P.steps.push_back(Step{name, [p, bt, bi, ni, skinny, sk](cudaStream_t s) {
+                               if constexpr (std::is_same<T, float>::value)
+                                 if (skinny)
+                                   return launch_gemm_tn_skinny<TAx>(p->table<G>(bt), p->table<GemmItem>(bi), ni, sk,
+                                                                     p->d_mats, s);
                                return launch_gemm_tn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
                                                                 p->d_mats, s);
                              }});
@@ -392,7 +405,11 @@ struct Builder {
         tag(3, ntask, gcols, 0, 0);
       }
     } else {
-      P.steps.push_back(Step{name, [p, bt, bi, ni](cudaStream_t s) {
+      P.steps.push_back(Step{name, [p, bt, bi, ni, skinny, sk](cudaStream_t s) {
+                               if constexpr (std::is_same<T, float>::value)
+                                 if (skinny)
+                                   return launch_gemm_nn_skinny<TAx>(p->table<G>(bt), p->table<GemmItem>(bi), ni, sk,
+                                                                     p->d_mats, s);
                                return launch_gemm_nn<TAx, T, T>(p->table<G>(bt), p->table<GemmItem>(bi), ni,
                                                                 p->d_mats, s);
                              }});
