@@ -704,6 +704,7 @@ struct Builder {
     T* R;       // kl x kl or nullptr
     T* G;
     T* R1;
+    T* R2;  // second-pass factor when the product R = R2 R1 is a separate GEMM
     T* Rinv;
   };
 
@@ -719,15 +720,20 @@ struct Builder {
     o.R = R;
     o.G = alloc<T>((size_t)kl * kl);
     o.R1 = R ? alloc<T>((size_t)kl * kl) : nullptr;
+    o.R2 = (R && sizeof(T) == 4) ? alloc<T>((size_t)kl * kl) : nullptr;
     o.Rinv = alloc<T>((size_t)kl * kl);
     return o;
   }
 
   void emit_orth(const std::string& name, const std::vector<OrthW>& ws, int passes, int kcapl) {
     if (ws.empty()) return;
+    // For 128-wide FP32 factors the product R = R2 R1 runs as its own GEMM:
+    // staging both triangles in the Cholesky kernel takes 132 KB of shared
+    // memory, one CTA per SM, and doubles the factorisation's time.
+    const bool sep_product = sizeof(T) == 4 && kcapl > 64 && passes == 2;
     for (int pass = 0; pass < passes; ++pass) {
       const bool last = pass == passes - 1;
-      std::vector<GS> gram, mult;
+      std::vector<GS> gram, mult, prod;
       std::vector<CholTask<T>> ch;
       for (const auto& w : ws) {
         const T* in = pass == 0 ? w.A : w.tmp;
@@ -745,6 +751,12 @@ struct Builder {
             c.R = w.R;
           } else if (pass == 0) {
             c.R = w.R1;
+          } else if (sep_product && w.R2) {
+            c.R = w.R2;
+            // R[0:k, 0:k] = R2 R1 over the live k only, as the fused product writes
+            GS g = nn(w.R2, w.kl, w.kl, w.k, w.R1, w.kl, w.k, w.R, w.kl);
+            g.M = w.k;
+            prod.push_back(g);
           } else {
             c.R = w.R;
             c.Rprev = w.R1;
@@ -759,6 +771,7 @@ struct Builder {
       const std::string tag = name + ".p" + std::to_string(pass + 1);
       emit_gemm(tag + ".gram", gram, true);
       emit_chol(tag + ".chol", ch, kcapl);
+      emit_gemm(tag + ".R", prod, false);
       emit_gemm(tag + ".mul", mult, false);
     }
   }
