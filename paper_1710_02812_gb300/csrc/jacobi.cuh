@@ -47,7 +47,17 @@ __device__ __forceinline__ float rsq(float x) {
   return r * fmaf(-0.5f * x, r * r, 1.5f);
 }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
+// Hardware reciprocal estimate (one MUFU operation, about 1 ulp).  It only
+// enters the rotation angle t: cs = rsq(1 + t^2) and sn = cs t make an
+// orthogonal rotation for any t, and an angle off by a few ulp leaves a
+// residual inner product of that relative size, far below the tolerance.
+// Its arguments are normal numbers (2c with c^2 > tol^2 ab > 0, and sums of
+// magnitudes at least that), so flushing subnormals changes nothing.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
 // Leading dimension of the column-major working copy: rows rounded up to the

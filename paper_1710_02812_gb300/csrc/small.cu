@@ -1238,22 +1238,73 @@ __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
   return d;
 }
 
-// One rotation of the column pair held by one group of 8 lanes (lane l holds
-// rows 4l..4l+3 of every chunk of 32 rows in x[] and y[]): inner products,
-// reduction over the group, rotation angle as in k_jacobi_sm, update in
-// registers.  Returns true (and cs, sn) when the pair was rotated.
-template <int RMAX, bool F2>
-__device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], float tol2, float big2, int& big,
+// Columns of a pair are held as packed FP32 pairs (lane l holds rows
+// 4l..4l+3 of every chunk of 32 rows: two 64-bit registers per chunk), so
+// loads, stores, shuffles and the f32x2 arithmetic all work on the packed
+// registers and no packing moves are needed.
+
+// sum of squares of a packed column, reduced over the 8-lane group
+template <int H>
+__device__ __forceinline__ float bp_sumsq(const uint64_t (&x)[H], unsigned gm) {
+  uint64_t s2[2] = {0, 0};
+#pragma unroll
+  for (int u = 0; u < H; ++u) s2[u & 1] = f2_fma(x[u], x[u], s2[u & 1]);
+  float lo, hi;
+  f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
+  float a = lo + hi;
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) a += __shfl_xor_sync(gm, a, off);
+  return a;
+}
+
+// Rotation angle of the pair from a = |x|^2, b = |y|^2, c = x.y, as in
+// k_jacobi_sm (the smaller-magnitude root t of t^2 + 2 zeta t - 1 = 0).
+// Returns false when the pair is already orthogonal to the tolerance.
+__device__ __forceinline__ bool bp_angle(float a, float b, float c, float tol2, float big2, int& big, float& t,
+                                         float& cs, float& sn) {
+  const float ab = a * b, cc = c * c;
+  if (!(ab > 0.f && cc > tol2 * ab)) return false;
+  big |= cc > big2 * ab;
+  const float zeta = (b - a) * fast_rcp(2.f * c);
+  const float az = fabsf(zeta);
+  if (az < 1e18f) {
+    const float q1 = 1.f + az * az;
+    t = fast_rcp(az + q1 * rsq(q1));
+  } else {
+    t = 0.5f * fast_rcp(az);
+  }
+  if (zeta < 0.f) t = -t;
+  cs = rsq(1.f + t * t);
+  sn = cs * t;
+  return true;
+}
+
+template <int H>
+__device__ __forceinline__ void bp_apply(uint64_t (&x)[H], uint64_t (&y)[H], float cs, float sn) {
+  const uint64_t cs2 = f2_pack(cs, cs), sn2 = f2_pack(sn, sn), nsn2 = f2_pack(-sn, -sn);
+#pragma unroll
+  for (int u = 0; u < H; ++u) {
+    const uint64_t x2 = x[u], y2 = y[u];
+    x[u] = f2_fma(cs2, x2, f2_mul(nsn2, y2));
+    y[u] = f2_fma(sn2, x2, f2_mul(cs2, y2));
+  }
+}
+
+// One rotation of the column pair held by one group of 8 lanes: inner
+// products, reduction over the group, rotation angle, update in registers.
+// Returns true (and cs, sn) when the pair was rotated.  F2 selects packed
+// f32x2 arithmetic; the scalar form is kept for comparison.
+template <int H, bool F2>
+__device__ __forceinline__ bool bp_rotate(uint64_t (&x)[H], uint64_t (&y)[H], float tol2, float big2, int& big,
                                           float& cs, float& sn) {
   float a, b, c;
   if constexpr (F2) {
     uint64_t a2[2] = {0, 0}, b2[2] = {0, 0}, c2[2] = {0, 0};
 #pragma unroll
-    for (int t = 0; t < RMAX / 2; ++t) {
-      const uint64_t x2 = f2_pack(xr[2 * t], xr[2 * t + 1]), y2 = f2_pack(yr[2 * t], yr[2 * t + 1]);
-      a2[t & 1] = f2_fma(x2, x2, a2[t & 1]);
-      b2[t & 1] = f2_fma(y2, y2, b2[t & 1]);
-      c2[t & 1] = f2_fma(x2, y2, c2[t & 1]);
+    for (int u = 0; u < H; ++u) {
+      a2[u & 1] = f2_fma(x[u], x[u], a2[u & 1]);
+      b2[u & 1] = f2_fma(y[u], y[u], b2[u & 1]);
+      c2[u & 1] = f2_fma(x[u], y[u], c2[u & 1]);
     }
     float lo, hi;
     f2_unpack(f2_add(a2[0], a2[1]), lo, hi);
@@ -1265,16 +1316,16 @@ __device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], 
   } else {
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, c0 = 0.f, c1 = 0.f;
 #pragma unroll
-    for (int t = 0; t < RMAX; ++t) {
-      if (t & 1) {
-        a1 = fmaf(xr[t], xr[t], a1);
-        b1 = fmaf(yr[t], yr[t], b1);
-        c1 = fmaf(xr[t], yr[t], c1);
-      } else {
-        a0 = fmaf(xr[t], xr[t], a0);
-        b0 = fmaf(yr[t], yr[t], b0);
-        c0 = fmaf(xr[t], yr[t], c0);
-      }
+    for (int u = 0; u < H; ++u) {
+      float x0, x1, y0, y1;
+      f2_unpack(x[u], x0, x1);
+      f2_unpack(y[u], y0, y1);
+      a0 = fmaf(x0, x0, a0);
+      b0 = fmaf(y0, y0, b0);
+      c0 = fmaf(x0, y0, c0);
+      a1 = fmaf(x1, x1, a1);
+      b1 = fmaf(y1, y1, b1);
+      c1 = fmaf(x1, y1, c1);
     }
     a = a0 + a1;
     b = b0 + b1;
@@ -1286,35 +1337,18 @@ __device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], 
     b += __shfl_xor_sync(0xffffffffu, b, off);
     c += __shfl_xor_sync(0xffffffffu, c, off);
   }
-  const float ab = a * b, cc = c * c;
-  if (!(ab > 0.f && cc > tol2 * ab)) return false;
-  big |= cc > big2 * ab;
-  const float zeta = (b - a) * fast_rcp(2.f * c);
-  const float az = fabsf(zeta);
   float t;
-  if (az < 1e18f) {
-    const float q1 = 1.f + az * az;
-    t = fast_rcp(az + q1 * rsq(q1));
-  } else {
-    t = 0.5f * fast_rcp(az);
-  }
-  if (zeta < 0.f) t = -t;
-  cs = rsq(1.f + t * t);
-  sn = cs * t;
+  if (!bp_angle(a, b, c, tol2, big2, big, t, cs, sn)) return false;
   if constexpr (F2) {
-    const uint64_t cs2 = f2_pack(cs, cs), sn2 = f2_pack(sn, sn), nsn2 = f2_pack(-sn, -sn);
-#pragma unroll
-    for (int u = 0; u < RMAX / 2; ++u) {
-      const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]), y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
-      f2_unpack(f2_fma(cs2, x2, f2_mul(nsn2, y2)), xr[2 * u], xr[2 * u + 1]);
-      f2_unpack(f2_fma(sn2, x2, f2_mul(cs2, y2)), yr[2 * u], yr[2 * u + 1]);
-    }
+    bp_apply<H>(x, y, cs, sn);
   } else {
 #pragma unroll
-    for (int u = 0; u < RMAX; ++u) {
-      const float xv = xr[u], yv = yr[u];
-      xr[u] = cs * xv - sn * yv;
-      yr[u] = sn * xv + cs * yv;
+    for (int u = 0; u < H; ++u) {
+      float x0, x1, y0, y1;
+      f2_unpack(x[u], x0, x1);
+      f2_unpack(y[u], y0, y1);
+      x[u] = f2_pack(cs * x0 - sn * y0, cs * x1 - sn * y1);
+      y[u] = f2_pack(sn * x0 + cs * y0, sn * x1 + cs * y1);
     }
   }
   return true;
@@ -1326,88 +1360,45 @@ __device__ __forceinline__ bool bp_rotate(float (&xr)[RMAX], float (&yr)[RMAX], 
 // A norm that falls below a quarter of its value is recomputed from the
 // rotated column (the update would cancel); all norms are recomputed at the
 // start of every sweep, so rounding does not accumulate past one sweep.
-template <int RMAX>
-__device__ __forceinline__ bool bp_rotate_nt(float (&xr)[RMAX], float (&yr)[RMAX], float& a, float& b, float tol2,
+template <int H>
+__device__ __forceinline__ bool bp_rotate_nt(uint64_t (&x)[H], uint64_t (&y)[H], float& a, float& b, float tol2,
                                              float big2, int& big, float& cs, float& sn, unsigned gm) {
   uint64_t c2[2] = {0, 0};
 #pragma unroll
-  for (int t = 0; t < RMAX / 2; ++t)
-    c2[t & 1] = f2_fma(f2_pack(xr[2 * t], xr[2 * t + 1]), f2_pack(yr[2 * t], yr[2 * t + 1]), c2[t & 1]);
+  for (int u = 0; u < H; ++u) c2[u & 1] = f2_fma(x[u], y[u], c2[u & 1]);
   float lo, hi;
   f2_unpack(f2_add(c2[0], c2[1]), lo, hi);
   float c = lo + hi;
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-  const float ab = a * b, cc = c * c;
-  if (!(ab > 0.f && cc > tol2 * ab)) return false;
-  big |= cc > big2 * ab;
-  const float zeta = (b - a) * fast_rcp(2.f * c);
-  const float az = fabsf(zeta);
   float t;
-  if (az < 1e18f) {
-    const float q1 = 1.f + az * az;
-    t = fast_rcp(az + q1 * rsq(q1));
-  } else {
-    t = 0.5f * fast_rcp(az);
-  }
-  if (zeta < 0.f) t = -t;
-  cs = rsq(1.f + t * t);
-  sn = cs * t;
-  const uint64_t cs2 = f2_pack(cs, cs), sn2 = f2_pack(sn, sn), nsn2 = f2_pack(-sn, -sn);
-#pragma unroll
-  for (int u = 0; u < RMAX / 2; ++u) {
-    const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]), y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
-    f2_unpack(f2_fma(cs2, x2, f2_mul(nsn2, y2)), xr[2 * u], xr[2 * u + 1]);
-    f2_unpack(f2_fma(sn2, x2, f2_mul(cs2, y2)), yr[2 * u], yr[2 * u + 1]);
-  }
+  if (!bp_angle(a, b, c, tol2, big2, big, t, cs, sn)) return false;
+  bp_apply<H>(x, y, cs, sn);
   const float tc = t * c;
   float an = a - tc, bn = b + tc;
-  if (!(an >= 0.25f * a)) {  // group-uniform: a, t, c are the same in the group's lanes
-    uint64_t s2[2] = {0, 0};
-#pragma unroll
-    for (int u = 0; u < RMAX / 2; ++u) {
-      const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]);
-      s2[u & 1] = f2_fma(x2, x2, s2[u & 1]);
-    }
-    f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
-    an = lo + hi;
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) an += __shfl_xor_sync(gm, an, off);
-  }
-  if (!(bn >= 0.25f * b)) {
-    uint64_t s2[2] = {0, 0};
-#pragma unroll
-    for (int u = 0; u < RMAX / 2; ++u) {
-      const uint64_t y2 = f2_pack(yr[2 * u], yr[2 * u + 1]);
-      s2[u & 1] = f2_fma(y2, y2, s2[u & 1]);
-    }
-    f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
-    bn = lo + hi;
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) bn += __shfl_xor_sync(gm, bn, off);
-  }
+  // group-uniform: a, t, c are the same in the group's lanes
+  if (!(an >= 0.25f * a)) an = bp_sumsq<H>(x, gm);
+  if (!(bn >= 0.25f * b)) bn = bp_sumsq<H>(y, gm);
   a = an;
   b = bn;
   return true;
 }
 
-template <int RMAX>
-__device__ __forceinline__ void bp_load(const float* Mw, int col, int ldm, int lane, float (&r)[RMAX]) {
-  const float4* p4 = reinterpret_cast<const float4*>(Mw + col * ldm) + lane;
+template <int H>
+__device__ __forceinline__ void bp_load(const float* Mw, int col, int ldm, int lane, uint64_t (&r)[H]) {
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(Mw + col * ldm) + lane;
 #pragma unroll
-  for (int t = 0; t < RMAX / 4; ++t) {
-    const float4 v = p4[t * 8];
-    r[4 * t] = v.x;
-    r[4 * t + 1] = v.y;
-    r[4 * t + 2] = v.z;
-    r[4 * t + 3] = v.w;
+  for (int t = 0; t < H / 2; ++t) {
+    const ulonglong2 v = p[t * 8];
+    r[2 * t] = v.x;
+    r[2 * t + 1] = v.y;
   }
 }
-template <int RMAX>
-__device__ __forceinline__ void bp_store(float* Mw, int col, int ldm, int lane, const float (&r)[RMAX]) {
-  float4* p4 = reinterpret_cast<float4*>(Mw + col * ldm) + lane;
+template <int H>
+__device__ __forceinline__ void bp_store(float* Mw, int col, int ldm, int lane, const uint64_t (&r)[H]) {
+  ulonglong2* p = reinterpret_cast<ulonglong2*>(Mw + col * ldm) + lane;
 #pragma unroll
-  for (int t = 0; t < RMAX / 4; ++t) p4[t * 8] = make_float4(r[4 * t], r[4 * t + 1], r[4 * t + 2], r[4 * t + 3]);
+  for (int t = 0; t < H / 2; ++t) p[t * 8] = make_ulonglong2(r[2 * t], r[2 * t + 1]);
 }
 __device__ __forceinline__ void bp_rotate_v(float* Vw, int ldv, int p, int q, int nc, int lane, float cs, float sn) {
   float* vx = Vw + p * ldv;
@@ -1440,6 +1431,7 @@ __global__ void __launch_bounds__(512, MINB) k_jacobi_bp(const JacobiTask<float>
   __shared__ float hh_scratch[520];
   __shared__ float nrm[128];  // squared column norms carried through a sweep (F2 path)
   constexpr int G = 8;
+  constexpr int H = RMAX / 2;  // packed FP32 pairs per lane and column
   constexpr int rows_pad = G * RMAX;
   const JacobiTask<float>& tk = tasks[blockIdx.x];
   int nr, nc, k1 = 0, k2 = 0;
@@ -1504,19 +1496,9 @@ __global__ void __launch_bounds__(512, MINB) k_jacobi_bp(const JacobiTask<float>
     int big = 0;
     if constexpr (F2) {  // exact squared norms at the start of the sweep
       for (int j = tid >> 3; j < n8; j += nt >> 3) {  // uniform per warp: n8, nt / 8 multiples of 4
-        float xr[RMAX];
-        bp_load<RMAX>(Mw, j, ldm, lane, xr);
-        uint64_t s2[2] = {0, 0};
-#pragma unroll
-        for (int u = 0; u < RMAX / 2; ++u) {
-          const uint64_t x2 = f2_pack(xr[2 * u], xr[2 * u + 1]);
-          s2[u & 1] = f2_fma(x2, x2, s2[u & 1]);
-        }
-        float lo, hi;
-        f2_unpack(f2_add(s2[0], s2[1]), lo, hi);
-        float a = lo + hi;
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) a += __shfl_xor_sync(gm8, a, off);
+        uint64_t xr[H];
+        bp_load<H>(Mw, j, ldm, lane, xr);
+        const float a = bp_sumsq<H>(xr, gm8);
         if (lane == 0) nrm[j] = a;
       }
       __syncthreads();
@@ -1531,29 +1513,29 @@ __global__ void __launch_bounds__(512, MINB) k_jacobi_bp(const JacobiTask<float>
         const int pa = h == 0 ? 0 : (t == 0 ? 2 : 1);
         const int pb = h == 0 ? t + 1 : (t == 2 ? 2 : 3);
         const int p = 4 * blk + pa, q = 4 * blk + pb;
-        float xr[RMAX], yr[RMAX];
+        uint64_t xr[H], yr[H];
         if (act) {
-          bp_load<RMAX>(Mw, p, ldm, lane, xr);
-          bp_load<RMAX>(Mw, q, ldm, lane, yr);
+          bp_load<H>(Mw, p, ldm, lane, xr);
+          bp_load<H>(Mw, q, ldm, lane, yr);
         } else {
 #pragma unroll
-          for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
+          for (int u = 0; u < H; ++u) xr[u] = yr[u] = 0;
         }
         float cs = 1.f, sn = 0.f;
         bool rot;
         if constexpr (F2) {
           float a = act ? nrm[p] : 0.f, b = act ? nrm[q] : 0.f;
-          rot = bp_rotate_nt<RMAX>(xr, yr, a, b, tol2, big2, big, cs, sn, gm8);
+          rot = bp_rotate_nt<H>(xr, yr, a, b, tol2, big2, big, cs, sn, gm8);
           if (act && rot && lane == 0) {
             nrm[p] = a;
             nrm[q] = b;
           }
         } else {
-          rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+          rot = bp_rotate<H, F2>(xr, yr, tol2, big2, big, cs, sn);
         }
         if (act && rot) {
-          bp_store<RMAX>(Mw, p, ldm, lane, xr);
-          bp_store<RMAX>(Mw, q, ldm, lane, yr);
+          bp_store<H>(Mw, p, ldm, lane, xr);
+          bp_store<H>(Mw, q, ldm, lane, yr);
           if (WANT_V) bp_rotate_v(Vw, ldv, p, q, nc, lane, cs, sn);
         }
         __syncwarp();
@@ -1564,41 +1546,41 @@ __global__ void __launch_bounds__(512, MINB) k_jacobi_bp(const JacobiTask<float>
     const bool wact = warp < nb / 2;  // warps past this core's block pairs idle
     for (int R = 0; R < nb - 1; ++R) {
       int I = 0, J = 0;
-      float xr[RMAX], yr[RMAX];
+      uint64_t xr[H], yr[H];
       float na = 0.f, nbb = 0.f;  // carried squared norms of the group's x and y columns (F2 path)
       if (wact) {
         rr_pair(nb, R, warp, I, J);
-        bp_load<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
-        bp_load<RMAX>(Mw, 4 * J + grp, ldm, lane, yr);
+        bp_load<H>(Mw, 4 * I + grp, ldm, lane, xr);
+        bp_load<H>(Mw, 4 * J + grp, ldm, lane, yr);
         if constexpr (F2) {
           na = nrm[4 * I + grp];
           nbb = nrm[4 * J + grp];
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < RMAX; ++u) xr[u] = yr[u] = 0.f;
+        for (int u = 0; u < H; ++u) xr[u] = yr[u] = 0;
       }
 #pragma unroll 1
       for (int t = 0; t < 4; ++t) {
         float cs = 1.f, sn = 0.f;
         bool rot;
         if constexpr (F2)
-          rot = bp_rotate_nt<RMAX>(xr, yr, na, nbb, tol2, big2, big, cs, sn, gm8);
+          rot = bp_rotate_nt<H>(xr, yr, na, nbb, tol2, big2, big, cs, sn, gm8);
         else
-          rot = bp_rotate<RMAX, F2>(xr, yr, tol2, big2, big, cs, sn);
+          rot = bp_rotate<H, F2>(xr, yr, tol2, big2, big, cs, sn);
         if (WANT_V) {
           if (wact && rot) bp_rotate_v(Vw, ldv, 4 * I + grp, 4 * J + ((grp + t) & 3), nc, lane, cs, sn);
           __syncwarp();
         }
         if (t < 3) {
 #pragma unroll
-          for (int u = 0; u < RMAX; ++u) yr[u] = __shfl_sync(0xffffffffu, yr[u], (tid + 8) & 31);
+          for (int u = 0; u < H; ++u) yr[u] = __shfl_sync(0xffffffffu, yr[u], (tid + 8) & 31);
           if constexpr (F2) nbb = __shfl_sync(0xffffffffu, nbb, (tid + 8) & 31);
         }
       }
       if (wact) {
-        bp_store<RMAX>(Mw, 4 * I + grp, ldm, lane, xr);
-        bp_store<RMAX>(Mw, 4 * J + ((grp + 3) & 3), ldm, lane, yr);
+        bp_store<H>(Mw, 4 * I + grp, ldm, lane, xr);
+        bp_store<H>(Mw, 4 * J + ((grp + 3) & 3), ldm, lane, yr);
         if (F2 && lane == 0) {
           nrm[4 * I + grp] = na;
           nrm[4 * J + ((grp + 3) & 3)] = nbb;
