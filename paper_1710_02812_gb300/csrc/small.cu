@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict_
   }
 
   int ndrop = 0;
+  const bool diag_up = tx >= ty;  // this thread's entries with a == b lie on or above the diagonal
   for (int j = 0; j < k; ++j) {
     const int buf = j & 1;
     const int aj = j >> 4;
@@ -324,24 +325,33 @@ __global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict_
     }
     // Rows i > j: upper entries (c >= i) and inverse entries (c < j) get
     // m[i][c] -= f_i m[j][c]; entry (i, j) becomes -f_i; the entries
-    // j < c < i (below the trailing diagonal) are left alone.
+    // j < c < i (below the trailing diagonal) are left alone.  Each case is
+    // one multiply-add: f_i is zero for rows i <= j; a lower entry (c < i)
+    // takes the multiplier m[j][c] for c < j, 1 for c == j (the entry is
+    // still zero, so it becomes -f_i) and 0 for c > j.  Whether an entry is
+    // upper is known at compile time off the tile's diagonal (b > a: upper,
+    // b < a: lower) and is tx >= ty on it.
     const T dinv = T(1) / d;
-    T f[KB], rj[KB];
-#pragma unroll
-    for (int a = 0; a < KB; ++a) f[a] = row[buf][ty + 16 * a] * dinv;
-#pragma unroll
-    for (int b = 0; b < KB; ++b) rj[b] = row[buf][tx + 16 * b];
+    T f[KB], ru[KB], rl[KB];
 #pragma unroll
     for (int a = 0; a < KB; ++a) {
       const int i = ty + 16 * a;
-      if (i <= j) continue;
+      f[a] = i > j ? row[buf][i] * dinv : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+      const int c = tx + 16 * b;
+      const T r = row[buf][c];
+      ru[b] = r;
+      rl[b] = c < j ? r : (c == j ? T(1) : T(0));
+    }
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      if (16 * a + (ty | 1) <= j) continue;  // warp-uniform: both rows of the warp are done
 #pragma unroll
       for (int b = 0; b < KB; ++b) {
-        const int c = tx + 16 * b;
-        if (c >= i || c < j)
-          m[a][b] -= f[a] * rj[b];
-        else if (c == j)
-          m[a][b] = -f[a];
+        const T r = b > a ? ru[b] : (b < a ? rl[b] : (diag_up ? ru[b] : rl[b]));
+        m[a][b] -= f[a] * r;
       }
     }
   }
