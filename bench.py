@@ -40,8 +40,8 @@ MODES = 512
 NOISE = 1e-5
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 # DRAM bytes per 128 x 128 core of k_jacobi_bp (ncu dram__bytes_read + dram__bytes_write of one
-# merge-level launch of the 2048^2 case: 473344 bytes for 8 cores)
-JACOBI_DRAM_BYTES_PER_CORE = 473344 / 8
+# merge-level launch of the 2048^2 case: 472576 bytes for 8 cores)
+JACOBI_DRAM_BYTES_PER_CORE = 472576 / 8
 
 
 def workload_config(prec, q):
