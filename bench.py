@@ -61,9 +61,11 @@ def set_size(size):
     MODES = min(512, size)
 
 
-def make_input():
+def make_input(rank=0):
+    """The bench matrix; rank r > 0 of a multi-GPU run draws its own
+    independent matrix of the same construction (seed tag 2 + 1000 r)."""
     from paper_1710_02812_gb300 import workloads as W
-    return W.exp_decay(M, N, MODES, NOISE, tag=2, dtype=np.float32)
+    return W.exp_decay(M, N, MODES, NOISE, tag=2 + 1000 * rank, dtype=np.float32)
 
 
 def peaks():
@@ -175,7 +177,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     x = make_input()
-    rows = 2048  # row band: 4 of the 16 slabs, every block / merge step of the path
+    rows = min(2048, M)  # row band: 4 of the 16 slabs, every block / merge step of the path
     for _ in range(args.warmup):
         oracle_run(x, rows)
     times = []
@@ -204,7 +206,7 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    x = make_input()
+    x = make_input(rank)
     xd = torch.from_numpy(x).to(dev)
     q = args.power_iters
     plan = hsvd.Plan(M, N, BR, BC, "fixed_k", K, prec=args.prec, power_iters=q, host_staging=True)
