@@ -123,3 +123,16 @@ def test_valid_plan_without_device_reports_cuda_error(lib):
     code, h = _plan_code(lib)
     assert code == hsvd.HSVD_ECUDA
     assert h.value is None
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libhsvd.so the binding raises on first use; nothing falls back
+    to a CPU implementation."""
+    monkeypatch.setattr(hsvd, "LIB_PATH", str(tmp_path / "libhsvd.so"))
+    monkeypatch.setattr(hsvd, "_lib_handle", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        hsvd.lib()
+    with pytest.raises(RuntimeError, match="no fallback"):
+        hsvd.Plan(64, 64, 32, 32, "fixed_k", 4, prec="f32")
+    with pytest.raises(RuntimeError, match="no fallback"):
+        hsvd.hsvd_tree_levels(5)
