@@ -36,7 +36,7 @@ typedef enum {
   HSVD_ENOMEM = 2,       /* device or host allocation failed */
   HSVD_ECUDA = 3,        /* a CUDA runtime call failed (launch, copy, no device) */
   HSVD_ENOTREADY = 4,    /* factors requested before any run */
-  HSVD_EUNSUPPORTED = 5  /* valid but not supported by this build (e.g. size) */
+  HSVD_EUNSUPPORTED = 5  /* valid but not supported by this library (e.g. size) */
 } hsvd_status;
 
 /* Truncation rule applied after every SVD on the path (Section 3: "MAT").

@@ -239,7 +239,7 @@ struct TcRedTask {
 };
 bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 cudaError_t launch_tc_reduce(const TcRedTask* tasks, const int2* items, int nitems, cudaStream_t s);
-bool tc_available();  // the driver's tensor-map encoder could be resolved
+bool tc_available();  // the CUDA driver's tensor-map encoder could be resolved
 
 // A factor B (K x N FP32, row-major, ld ldb) written as its BF16 transpose:
 // `bmax` rows of `kpad` columns at hi (and the low parts at lo, if not null).

@@ -1,4 +1,4 @@
-// Conversions of the BF16-mixed path (SURVEY step a1 and the operand
+// Conversions of the BF16-mixed path (the input conversion and the operand
 // preparation of the tensor-core products):
 //  * k_convert_input: the input (FP32 or BF16, row-major) -> plan-owned BF16
 //    copies X (m x ldx) and X^T (n x ldxt), rounding to nearest even, through

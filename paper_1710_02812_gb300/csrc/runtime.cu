@@ -1407,7 +1407,7 @@ const char* hsvd_error_string(hsvd_status s) {
     case HSVD_ENOMEM: return "out of memory";
     case HSVD_ECUDA: return "CUDA runtime error";
     case HSVD_ENOTREADY: return "no run has completed on this plan";
-    case HSVD_EUNSUPPORTED: return "not supported by this build";
+    case HSVD_EUNSUPPORTED: return "not supported by this library";
   }
   return "unknown status";
 }
@@ -1518,7 +1518,7 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   P.mixed = prec == HSVD_PREC_BF16_MIXED;
   // Tensor-core products need the block origins on 8-element (16-byte)
   // boundaries for TMA, a sketch of at most 256 columns, and the tensor-map
-  // encoder of the driver.
+  // encoder of the CUDA driver.
   P.graph_off = std::getenv("HSVD_NO_GRAPH") != nullptr;
   P.use_tc = P.mixed && block_rows % 8 == 0 && block_cols % 8 == 0 && P.kp <= 256 && !std::getenv("HSVD_NO_TC") &&
              hsvd::tc_available();
