@@ -209,7 +209,7 @@ hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r);
 hsvd_status hsvd_factors(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* U, int64_t ldu,
                          void* S, void* V, int64_t ldv, hsvd_where where, void* stream);
 
-/* hsvd_workspace_bytes -- device bytes the plan holds (host query). */
+/* hsvd_workspace_bytes -- device bytes the plan holds (host query; 0 for NULL). */
 int64_t hsvd_workspace_bytes(hsvd_plan_t plan);
 
 /* hsvd_launches_per_run -- number of kernel launches one hsvd_run enqueues

@@ -136,3 +136,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         hsvd.Plan(64, 64, 32, 32, "fixed_k", 4, prec="f32")
     with pytest.raises(RuntimeError, match="no fallback"):
         hsvd.hsvd_tree_levels(5)
+
+
+def test_plain_c_client_builds_and_runs_host_entry_points(lib, tmp_path):
+    """The header is plain C99: a C client compiles with -pedantic -Werror,
+    links against libhsvd.so and runs the entry points that need no device."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "c_abi_client"
+    libdir = os.path.dirname(hsvd.LIB_PATH)
+    cmd = [cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c_abi_client.c"), "-o", str(exe), "-L", libdir, "-lhsvd",
+           "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
