@@ -1,6 +1,12 @@
-"""Build libhsvd.so in-tree with nvcc for sm_103a (no cmake, parallel TUs)."""
+"""Build libhsvd.so in-tree with nvcc for sm_103a (no cmake, parallel TUs).
+
+Safe to call from several processes at once (one per rank of a multi-GPU
+run): the build holds an exclusive lock on a file in the build folder, so
+the first caller compiles and the others wait and then find the library up
+to date."""
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -41,6 +47,15 @@ def _compile(src: str, verbose: bool) -> str:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, force)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, force: bool) -> str:
     srcs = sources()
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     hdrs.append(os.path.join(PKG, "..", "include", "hsvd.h"))
