@@ -387,3 +387,28 @@ def test_iterative_improvement_reduces_the_mat_error():
     ref = oracle.iterative_improvement(x, res.v, res.s, eps=1e-3, max_iters=20)
     after = H.relative_error(xk, (ref.u * ref.s) @ ref.v.T)
     assert before > 1e-4 and after < 0.8 * before, (before, after)
+
+
+def test_trace_records_every_rank_decision_and_its_margin():
+    """X = diag(10, 5, 1, 0.5) on a 2 x 2 grid, gamma = 0.1, derived by hand:
+    the diagonal blocks keep both values (nearest to their thresholds 1 and
+    0.1: 5 and 0.5, margin 0.4 of sigma_1), the off-diagonal blocks are zero
+    (rank 0, no margin), each slab's merge and slab step repeat its block,
+    and the row merge sees 10, 5, 1, 0.5 against the threshold 1: it keeps
+    three and the deciding value 1 sits exactly on the threshold (margin 0,
+    the tie a parity run must flag)."""
+    x = np.diag([10.0, 5.0, 1.0, 0.5])
+    res = oracle.hmat_svd(x, 2, 2, Rule("gamma", 0.1))
+    names = [t[0] for t in res.trace.steps]
+    ranks = [t[1] for t in res.trace.steps]
+    margins = [t[2] for t in res.trace.steps]
+    assert names == ["block0,0", "block0,1", "col0L0#0", "slab0",
+                     "block1,0", "block1,1", "col1L0#0", "slab1", "rowL0#0"]
+    assert ranks == [2, 0, 2, 2, 0, 2, 2, 2, 3]
+    want = [0.4, None, 0.4, 0.4, None, 0.4, 0.4, 0.4, 0.0]
+    for got, w in zip(margins, want):
+        if w is None:
+            assert np.isnan(got)
+        else:
+            assert got == pytest.approx(w, abs=1e-15)
+    np.testing.assert_allclose(res.s, [10.0, 5.0, 1.0], rtol=0, atol=1e-14)
