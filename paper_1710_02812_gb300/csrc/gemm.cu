@@ -457,7 +457,6 @@ __global__ void __launch_bounds__(256) k_gemm2_reduce(const GemmTask<TA, float, 
 // padding (narrow blocks and low-rank merges), so these kernels size the work
 // to the product.  Items and split-K partials keep k_gemm2's layout (one
 // 128 x 64 tile per task), so the same reduction kernel applies.
-constexpr int SK = 32;
 
 // TN: C (M x N) = A^T B over a K chunk; A: K x M, B: K x N (row-major),
 // M, N <= SK.  64-row slabs of A and B staged in shared memory; the SK x SK

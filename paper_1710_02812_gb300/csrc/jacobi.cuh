@@ -78,5 +78,87 @@ __host__ __device__ __forceinline__ int jacobi_ld_g(int nr, int elem, int G) {
   return ld;
 }
 
+// Sort the singular values (column norms in sig_s), choose the rank by the
+// truncation rule and write sigma, the normalised left vectors and, if
+// wanted, the sorted right rotations.
+template <class T, bool WANT_V>
+__device__ void jacobi_finish(const JacobiTask<T>& tk, const T* Mw, int ldm, const T* Vw, int ldv, int nr, int nc,
+                              int k1, int k2, const TruncParams& tp, DevStatus* st, T* sig_s, int* perm,
+                              int* rank_sp) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = tid; j < nc; j += nt) {
+    const T sj = sig_s[j];
+    int pos = 0;
+    for (int i = 0; i < nc; ++i) {
+      const T si = sig_s[i];
+      pos += (si > sj) || (si == sj && i < j);
+    }
+    perm[pos] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int bad = 0;
+    for (int i = 0; i < nc; ++i) bad += sig_s[i] < T(0);
+    if (bad && st) atomicAdd(&st->nonfinite, 1);
+    int r = 0;
+    const double s1 = nc > 0 ? (double)sig_s[perm[0]] : 0.0;
+    if (nc > 0 && s1 > 0.0 && !bad) {
+      int numerical = 0;
+      for (int i = 0; i < nc; ++i) numerical += (double)sig_s[perm[i]] > tp.rank_tol * s1;
+      if (tp.mode == 0) {
+        r = (int)tp.param;
+      } else if (tp.mode == 1) {
+        r = 0;
+        for (int i = 0; i < nc; ++i) r += (double)sig_s[perm[i]] >= tp.param * s1;
+      } else {
+        double total = 0.0;
+        if (tk.energy) {
+          total = (double)*tk.energy;
+        } else if (tk.load == 1) {
+          for (int i = 0; i < k1; ++i) total += (double)tk.s1[i] * (double)tk.s1[i];
+          for (int i = 0; i < k2; ++i) total += (double)tk.s2[i] * (double)tk.s2[i];
+        } else {
+          for (int i = 0; i < nc; ++i) total += (double)sig_s[i] * (double)sig_s[i];
+        }
+        double cum = 0.0;
+        r = nc;
+        for (int i = 0; i < nc; ++i) {
+          const double s = (double)sig_s[perm[i]];
+          cum += s * s;
+          if (cum >= tp.param * total) {
+            r = i + 1;
+            break;
+          }
+        }
+      }
+      r = min(r, numerical);
+      r = min(r, tp.rank_cap);
+      r = min(r, nc);
+      r = min(r, tk.ucap);
+      if (r < 0) r = 0;
+    }
+    *rank_sp = r;
+    if (tk.rank) *tk.rank = r;
+  }
+  __syncthreads();
+  const int r = *rank_sp;
+  if (tk.sig)
+    for (int c = tid; c < tk.ucap; c += nt) tk.sig[c] = (c < r) ? sig_s[perm[c]] : T(0);
+  if (tk.U) {
+    for (int e = tid; e < nr * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      T v = T(0);
+      if (c < r) v = Mw[(int64_t)perm[c] * ldm + i] / sig_s[perm[c]];
+      tk.U[(int64_t)i * tk.ldu + c] = v;
+    }
+  }
+  if (WANT_V && tk.V) {
+    for (int e = tid; e < nc * tk.ucap; e += nt) {
+      const int i = e / tk.ucap, c = e % tk.ucap;
+      tk.V[(int64_t)i * tk.ldv + c] = (c < r) ? Vw[(int64_t)perm[c] * ldv + i] : T(0);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace hsvd
