@@ -1,6 +1,7 @@
 // Device helpers shared by the core-SVD kernels (one-sided Jacobi): machine
 // epsilon per type, the round-robin pair ordering, the refined reciprocal
-// square root and the padded leading dimensions of the working copies.
+// square root, the padded leading dimensions of the working copies, and
+// jacobi_finish, the common end of a core (sort, truncation rule, output).
 #pragma once
 
 #include "common.cuh"
