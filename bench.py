@@ -380,7 +380,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16_mixed", choices=["f32", "bf16_mixed", "f64"])
+    ap.add_argument("--prec", default="bf16_mixed", choices=["f32", "bf16_mixed"],
+                    help="path timed: the BF16-mixed headline or the plain FP32 path (the metric compares the two)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparison run")
     ap.add_argument("--power-iters", dest="power_iters", type=int, default=1)
     ap.add_argument("--no-oracle", action="store_true")

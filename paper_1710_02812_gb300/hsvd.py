@@ -130,6 +130,65 @@ def _stream_ptr(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+# ------------------------------------------------------------------ argument checks
+# The C ABI receives raw pointers: the kernels read m x n elements of the
+# planned type from each input and write kcap-column factors, so a buffer of
+# the wrong size or element type would be read or written past its end.  The
+# binding checks what the C side cannot see before any call.
+
+def _torch_dtype(name: str):
+    import torch
+    return {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[name]
+
+
+def check_inputs(mats, ms, ns, in_dtype: str, device: bool) -> None:
+    """Inputs of hsvd_run (device=True: CUDA tensors) or hsvd_run_host
+    (device=False: numpy arrays or CPU tensors): one 2-D matrix per planned
+    matrix, of the planned shape and element type, with contiguous rows."""
+    import torch
+    if len(mats) != len(ms):
+        raise ValueError(f"{len(mats)} matrices given, the plan holds {len(ms)}")
+    want = _torch_dtype(in_dtype)
+    for i, (t, m, n) in enumerate(zip(mats, ms, ns)):
+        if isinstance(t, np.ndarray):
+            if device:
+                raise TypeError(f"matrix {i}: hsvd_run reads device memory; pass a CUDA tensor")
+            if t.ndim != 2 or t.shape != (m, n):
+                raise ValueError(f"matrix {i}: shape {t.shape}, the plan expects {(m, n)}")
+            if in_dtype == "bf16" or t.dtype != np.dtype(np.float64 if in_dtype == "f64" else np.float32):
+                raise TypeError(f"matrix {i}: dtype {t.dtype}, the plan expects {want}")
+            if (n > 1 and t.strides[1] != t.itemsize) or (m > 1 and t.strides[0] < n * t.itemsize):
+                raise ValueError(f"matrix {i}: rows must be contiguous (strides {t.strides})")
+            continue
+        if not isinstance(t, torch.Tensor) or t.dim() != 2:
+            raise TypeError(f"matrix {i}: a 2-D tensor is required")
+        if tuple(t.shape) != (m, n):
+            raise ValueError(f"matrix {i}: shape {tuple(t.shape)}, the plan expects {(m, n)}")
+        if t.dtype != want:
+            raise TypeError(f"matrix {i}: dtype {t.dtype}, the plan expects {want}")
+        if (n > 1 and t.stride(1) != 1) or (m > 1 and t.stride(0) < n):
+            raise ValueError(f"matrix {i}: rows must be contiguous (strides {t.stride()})")
+        if t.is_cuda != device:
+            raise ValueError(f"matrix {i}: " + ("hsvd_run reads device memory; pass a CUDA tensor" if device
+                                                else "hsvd_run_host reads host memory; pass a CPU array"))
+
+
+def check_factor_outputs(U, S, V, kcap: int, m: int, n: int, factor_dtype: str) -> None:
+    """Device outputs of hsvd_factors: contiguous CUDA tensors of the factor
+    type holding at least kcap x m (U), kcap (S) and kcap x n (V) elements."""
+    import torch
+    want = _torch_dtype(factor_dtype)
+    for name, t, need in (("U", U, kcap * m), ("S", S, kcap), ("V", V, kcap * n)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name}: a CUDA tensor is required")
+        if t.dtype != want:
+            raise TypeError(f"{name}: dtype {t.dtype}, the plan's factors are {want}")
+        if not t.is_contiguous() or t.numel() < need:
+            raise ValueError(f"{name}: a contiguous tensor of at least {need} elements is required")
+
+
 # ------------------------------------------------------------------ C names
 
 def hsvd_plan(m: Sequence[int], n: Sequence[int], block_rows: int, block_cols: int, mode: str = "fixed_k",
@@ -314,12 +373,14 @@ class Plan:
 
     def run(self, mats, stream=None):
         """mats: list of CUDA tensors (row-major, contiguous rows)."""
+        check_inputs(mats, self.m, self.n, self.in_dtype, device=True)
         ptrs = [t.data_ptr() for t in mats]
         lda = [t.stride(0) for t in mats]
         hsvd_run(self._h, ptrs, lda, stream)
 
     def run_host(self, arrays, stream=None):
         """arrays: list of host arrays (numpy or CPU tensors)."""
+        check_inputs(arrays, self.m, self.n, self.in_dtype, device=False)
         ptrs, lda = [], []
         for a in arrays:
             if isinstance(a, np.ndarray):
@@ -348,6 +409,7 @@ class Plan:
     def factors_device(self, U, S, V, idx=0, stream=None) -> int:
         """Write column-major factors into device tensors U (kcap x m storage),
         S (kcap), V (kcap x n storage); returns the rank."""
+        check_factor_outputs(U, S, V, self.kcap, self.m[idx], self.n[idx], "f64" if self.prec == "f64" else "f32")
         r = ctypes.c_int32()
         code = hsvd_factors(self._h, idx, ctypes.byref(r), U.data_ptr() if U is not None else None, self.m[idx],
                             S.data_ptr() if S is not None else None, V.data_ptr() if V is not None else None,

@@ -156,3 +156,56 @@ def test_plain_c_client_builds_and_runs_host_entry_points(lib, tmp_path):
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def _planless(m, n, in_dtype="f32", prec="f32", kcap=4):
+    """A Plan object with the planned sizes but no device plan: any library
+    call would fail, so an error here must come from the binding's checks."""
+    p = object.__new__(hsvd.Plan)
+    p.m, p.n, p.in_dtype, p.prec, p.kcap = list(m), list(n), in_dtype, prec, kcap
+    p._h = None
+    return p
+
+
+def test_binding_rejects_inputs_the_kernels_would_overrun():
+    import numpy as np
+    import torch
+    p = _planless([6, 5], [4, 3])
+    good = [torch.zeros(6, 4), torch.zeros(5, 3)]
+    with pytest.raises(ValueError, match="the plan holds 2"):
+        hsvd.check_inputs(good[:1], p.m, p.n, "f32", device=False)
+    with pytest.raises(ValueError, match="shape"):
+        hsvd.check_inputs([torch.zeros(6, 4), torch.zeros(4, 3)], p.m, p.n, "f32", device=False)
+    with pytest.raises(TypeError, match="dtype"):
+        hsvd.check_inputs([torch.zeros(6, 4, dtype=torch.float64), good[1]], p.m, p.n, "f32", device=False)
+    with pytest.raises(TypeError, match="dtype"):  # an f32 buffer for an f64 plan is half the bytes
+        hsvd.check_inputs(good, p.m, p.n, "f64", device=False)
+    with pytest.raises(ValueError, match="contiguous"):
+        hsvd.check_inputs([torch.zeros(4, 6).t(), good[1]], p.m, p.n, "f32", device=False)
+    with pytest.raises(TypeError, match="2-D"):
+        hsvd.check_inputs([torch.zeros(24), good[1]], p.m, p.n, "f32", device=False)
+    hsvd.check_inputs(good, p.m, p.n, "f32", device=False)                 # host inputs are fine
+    hsvd.check_inputs([np.zeros((6, 4), np.float32), np.zeros((5, 3), np.float32)], p.m, p.n, "f32",
+                      device=False)
+    wide = torch.zeros(6, 10)[:, 2:6]                                        # ld 10 > n 4: allowed
+    hsvd.check_inputs([wide, good[1]], p.m, p.n, "f32", device=False)
+    with pytest.raises(TypeError, match="dtype"):                          # numpy has no bf16
+        hsvd.check_inputs([np.zeros((6, 4), np.float32), np.zeros((5, 3), np.float32)], p.m, p.n, "bf16",
+                          device=False)
+    # run() checks before any library call; host tensors are not device memory
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        p.run(good)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        p.run([np.zeros((6, 4), np.float32), np.zeros((5, 3), np.float32)])
+    with pytest.raises(ValueError, match="shape"):
+        p.run_host([np.zeros((5, 4), np.float32), np.zeros((5, 3), np.float32)])
+
+
+def test_binding_rejects_factor_outputs_too_small_or_of_the_wrong_type():
+    import torch
+    p = _planless([6], [4], kcap=3)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        p.factors_device(torch.zeros(3, 6), None, None)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        hsvd.check_factor_outputs(None, torch.zeros(3), None, 3, 6, 4, "f32")
+    hsvd.check_factor_outputs(None, None, None, 3, 6, 4, "f32")             # nothing requested
