@@ -240,11 +240,17 @@ def hsvd_gram(X, G, stream=None):
     """G = X^T X on the device (torch tensors: X m x n, G n x n, both float32 or
     both float64, row-major with unit column stride)."""
     import torch
+    if X.dim() != 2 or G.dim() != 2:
+        raise TypeError("X and G must be 2-D tensors")
     if X.dtype != G.dtype or X.dtype not in (torch.float32, torch.float64):
         raise TypeError("X and G must both be float32 or both float64")
-    if X.stride(1) != 1 or G.stride(1) != 1:
-        raise ValueError("rows must be contiguous")
     m, n = X.shape
+    if tuple(G.shape) != (n, n):
+        raise ValueError(f"G must be {n} x {n} for X of {m} x {n}, got {tuple(G.shape)}")
+    if X.stride(1) != 1 or G.stride(1) != 1 or X.stride(0) < n or G.stride(0) < n:
+        raise ValueError("rows must be contiguous")
+    if not (X.is_cuda and G.is_cuda):
+        raise ValueError("X and G must be CUDA tensors")
     prec = PREC["f64"] if X.dtype == torch.float64 else PREC["f32"]
     _check(lib().hsvd_gram(X.data_ptr(), X.stride(0), m, n, prec, G.data_ptr(), G.stride(0), _stream_ptr(stream)),
            "hsvd_gram")

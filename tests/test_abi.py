@@ -209,3 +209,14 @@ def test_binding_rejects_factor_outputs_too_small_or_of_the_wrong_type():
     with pytest.raises(TypeError, match="CUDA tensor"):
         hsvd.check_factor_outputs(None, torch.zeros(3), None, 3, 6, 4, "f32")
     hsvd.check_factor_outputs(None, None, None, 3, 6, 4, "f32")             # nothing requested
+
+
+def test_gram_binding_rejects_mismatched_buffers():
+    import torch
+    x = torch.zeros(8, 5)
+    with pytest.raises(ValueError, match="5 x 5"):
+        hsvd.hsvd_gram(x, torch.zeros(4, 4))
+    with pytest.raises(TypeError, match="float32"):
+        hsvd.hsvd_gram(x, torch.zeros(5, 5, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        hsvd.hsvd_gram(x, torch.zeros(5, 5))
