@@ -63,6 +63,24 @@ def planted(m: int, n: int, s, noise: float = 0.0, tag: int = 0,
     return a
 
 
+def planted_band(m: int, n: int, s, noise: float = 0.0, tag: int = 0, rows: int = 1, cols: int = 1,
+                 dtype=np.float32):
+    """Rows 0..rows and columns 0..cols of ``planted(m, n, s, noise, tag)``
+    without building the m x n matrix: the same U, V and noise stream (the
+    generator fills row by row, so the first rows x n draws are the noise of
+    the first rows).  Equal to the slice of the full matrix up to the rounding
+    order of the product."""
+    s = np.asarray(s, dtype=np.float64)
+    r = s.shape[0]
+    g = rng(tag)
+    u = orthonormal(g, m, r)
+    v = orthonormal(g, n, r)
+    a = (u[:rows] * s[None, :]) @ v[:cols].T
+    if noise:
+        a += noise * g.standard_normal((rows, n))[:, :cols]
+    return np.ascontiguousarray(a.astype(dtype))
+
+
 def fixed_rank_512(dtype=np.float64):
     """512^2, r = 10, s_i = 10^(-i/3), noise 1e-6 (the FP64 parity case)."""
     s = 10.0 ** (-np.arange(10) / 3.0)
@@ -201,11 +219,14 @@ def power_law_65536(device="cuda"):
 
 
 def pod_fourier_device(m: int = 32768, n: int = 16384, modes: int = 40, noise: float = 1e-3,
-                       tag: int = 3, device="cuda", chunk_rows: int = 4096, stats=None):
+                       tag: int = 3, device="cuda", chunk_rows: int = 4096, stats=None,
+                       keep_rounding: bool = False):
     """pod_fourier on the device, BF16 storage; also returns the coefficient
     matrix C (modes x n, FP64 on the host), whose singular values are those of
     the noise-free part (the modes are orthonormal).  stats (a dict), if
-    given, receives the Frobenius norm of the BF16 storage rounding."""
+    given, receives the Frobenius norm of the BF16 storage rounding and, with
+    keep_rounding, the rounding itself (stored BF16 value minus the FP32
+    snapshot, m x n FP32 on the device) under "rounding"."""
     import torch
     g = _torch_gen(tag, device)
     xg = torch.arange(m, dtype=torch.float64, device=device) / m
@@ -219,14 +240,20 @@ def pod_fourier_device(m: int = 32768, n: int = 16384, modes: int = 40, noise: f
     phif, cf = phi.to(torch.float32), c.to(torch.float32)
     a = torch.empty((m, n), dtype=torch.bfloat16, device=device)
     rounding2 = 0.0
+    rnd = torch.empty((m, n), dtype=torch.float32, device=device) if keep_rounding else None
     for r0 in range(0, m, chunk_rows):
         r1 = min(m, r0 + chunk_rows)
         blk = phif[r0:r1] @ cf
         blk += noise * torch.randn((r1 - r0, n), generator=g, device=device, dtype=torch.float32)
         a[r0:r1] = blk.to(torch.bfloat16)
-        rounding2 += float(((a[r0:r1].float() - blk).double() ** 2).sum())
+        d = a[r0:r1].float() - blk
+        rounding2 += float((d.double() ** 2).sum())
+        if rnd is not None:
+            rnd[r0:r1] = d
     if stats is not None:
         stats["rounding_fro"] = rounding2 ** 0.5
+        if rnd is not None:
+            stats["rounding"] = rnd
     return a, c.cpu().numpy()
 
 

@@ -129,6 +129,34 @@ def test_fp64_row_then_col():
     check(x, got, ref, "f64", "row_then_col", s_true=np.linalg.svd(x, compute_uv=False)[:10])
 
 
+def _largest_entry_positive(u):
+    """The output sign rule: the largest-magnitude entry of each U column is
+    positive."""
+    idx = np.argmax(np.abs(u), axis=0)
+    return bool(np.all(u[idx, np.arange(u.shape[1])] > 0))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16_mixed"])
+@pytest.mark.parametrize("tree", ["col_then_row", "row_then_col"])
+def test_signs_match_oracle_elementwise(prec, tree):
+    """U and V compared entry by entry WITH their signs (no abs, no angles): on
+    an exactly rank-6 input with well separated values every singular vector
+    is unique up to sign, so the device's sign normalisation must give the
+    oracle's vectors themselves.  The rule (largest-magnitude entry of each U
+    column positive) is also checked on the device output directly."""
+    s = np.array([4.0, 2.5, 1.6, 1.0, 0.6, 0.35])
+    x = W.planted(296, 264, s, noise=0.0, tag=31)
+    xin = W.bf16_round(x) if prec == "bf16_mixed" else x
+    (got,), st, _ = run_gpu([xin], 80, 72, "fixed_k", 6, prec, tree=tree)
+    u, sg, v = got
+    ref = oracle_run(xin, 80, 72, "fixed_k", 6, prec, tree=tree)
+    assert sg.size == ref.s.size == 6
+    assert _largest_entry_positive(u)
+    tol = 1e-10 if prec == "f64" else 1e-3
+    np.testing.assert_allclose(u, ref.u, rtol=0, atol=tol)
+    np.testing.assert_allclose(v, ref.v, rtol=0, atol=tol)
+
+
 # ---------------------------------------------------------------- FP32
 
 @pytest.mark.parametrize("m,n,br,bc,k", [

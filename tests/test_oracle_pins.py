@@ -412,3 +412,64 @@ def test_trace_records_every_rank_decision_and_its_margin():
         else:
             assert got == pytest.approx(w, abs=1e-15)
     np.testing.assert_allclose(res.s, [10.0, 5.0, 1.0], rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- sign convention
+
+def test_normalise_signs_hand_built_columns():
+    """Sign rule of the output (the largest-magnitude entry of each U column is
+    made positive, the first such entry on ties; V follows U): expected arrays
+    written out by hand, including a negative maximum, a tie whose first entry
+    is negative, a tie whose first entry is positive and a zero column."""
+    u = np.array([[0.1, 0.5, -0.6, 0.4, 0.0],
+                  [-0.9, 0.1, 0.6, -0.4, 0.0],
+                  [0.3, -0.2, 0.1, 0.0, 0.0],
+                  [0.2, 0.7, 0.0, 0.0, 0.0]])
+    v = np.array([[1.0, 2.0, 3.0, 4.0, 5.0],
+                  [-1.0, -2.0, -3.0, -4.0, -5.0]])
+    s = np.array([5.0, 4.0, 3.0, 2.0, 0.0])
+    un, sn, vn = H.normalise_signs(u, s, v)
+    u_expect = np.array([[-0.1, 0.5, 0.6, 0.4, 0.0],
+                         [0.9, 0.1, -0.6, -0.4, 0.0],
+                         [-0.3, -0.2, -0.1, 0.0, 0.0],
+                         [-0.2, 0.7, 0.0, 0.0, 0.0]])
+    v_expect = np.array([[-1.0, 2.0, -3.0, 4.0, 5.0],
+                         [1.0, -2.0, 3.0, -4.0, -5.0]])
+    np.testing.assert_array_equal(un, u_expect)
+    np.testing.assert_array_equal(vn, v_expect)
+    np.testing.assert_array_equal(sn, s)
+
+
+def test_sign_convention_worked_example():
+    """A = [[0, -2], [3, 0], [0, 0]]: sigma = (3, 2); the rule fixes
+    u1 = e2, v1 = e1 (A v1 = 3 u1) and u2 = e1, v2 = -e2 (A v2 = 2 u2), on
+    every grid and in both tree orders."""
+    a = np.array([[0.0, -2.0], [3.0, 0.0], [0.0, 0.0]])
+    u_expect = np.array([[0.0, 1.0], [1.0, 0.0], [0.0, 0.0]])
+    v_expect = np.array([[1.0, 0.0], [0.0, -1.0]])
+    for br, bc in [(3, 2), (1, 1), (2, 1), (1, 2)]:
+        for tree in ("col_then_row", "row_then_col"):
+            res = H.hmat_svd(a, br, bc, Rule(H.FIXED_K, 2), tree=tree)
+            np.testing.assert_allclose(res.s, [3.0, 2.0], rtol=1e-14)
+            np.testing.assert_allclose(res.u, u_expect, atol=1e-14)
+            np.testing.assert_allclose(res.v, v_expect, atol=1e-14)
+
+
+def test_sign_convention_permuted_diagonal():
+    """For a permuted diagonal matrix with entries of both signs every
+    singular vector is a signed unit vector: the rule makes each u a +e_p and
+    gives v the sign of the diagonal entry (A v = sigma u)."""
+    g = np.random.default_rng(11)
+    d = (np.arange(12, 0, -1, dtype=np.float64) + 0.5) * g.choice([-1.0, 1.0], 12)
+    rows, cols = g.permutation(16)[:12], g.permutation(14)[:12]
+    a = np.zeros((16, 14))
+    a[rows, cols] = d
+    for br, bc, tree in [(16, 14, "col_then_row"), (5, 4, "col_then_row"), (4, 5, "row_then_col")]:
+        res = H.hmat_svd(a, br, bc, Rule(H.FIXED_K, 6), tree=tree)
+        for i in range(6):
+            u_e = np.zeros(16)
+            u_e[rows[i]] = 1.0
+            v_e = np.zeros(14)
+            v_e[cols[i]] = np.sign(d[i])
+            np.testing.assert_allclose(res.u[:, i], u_e, atol=1e-13)
+            np.testing.assert_allclose(res.v[:, i], v_e, atol=1e-13)

@@ -58,3 +58,10 @@ def test_planted_factors_are_what_they_claim():
     np.testing.assert_allclose(v.T @ v, np.eye(20), atol=1e-13)
     np.testing.assert_allclose(a, (u * s_out) @ v.T, atol=1e-13)
     np.testing.assert_allclose(np.linalg.svd(a, compute_uv=False)[:20], np.sort(s)[::-1], rtol=1e-12)
+
+
+def test_planted_band_is_the_slice_of_the_full_matrix():
+    s = (np.arange(40) + 1.0) ** -1.5
+    full = W.planted(300, 260, s, noise=1e-6, tag=77, dtype=np.float64)
+    band = W.planted_band(300, 260, s, noise=1e-6, tag=77, rows=48, cols=100, dtype=np.float64)
+    np.testing.assert_allclose(band, full[:48, :100], rtol=0, atol=1e-15)
