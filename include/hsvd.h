@@ -263,6 +263,13 @@ hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* ru
  *           are written (r = the rank, numerically zero values dropped)
  *   S       device, k FP32 singular values, descending, zero past r
  *   rank    device int32 receiving r
+ *   flags   device int32 receiving the call's status bits, or NULL:
+ *           1 = the Jacobi core hit its sweep cap (not converged),
+ *           2 = CholeskyQR dropped numerically dependent directions (a
+ *               rank-deficient block; the result is still valid),
+ *           4 = a NaN or Inf was met (U, S and rank are not meaningful).
+ *           0 means a clean run.  The same words hsvd_status_query reports
+ *           for a plan.
  * Asynchronous on `stream`.  Sizes beyond the limits return
  * HSVD_EUNSUPPORTED; bad pointers or shapes HSVD_EINVAL.  The first call on
  * a device resolves the array's device address (cudaGetSymbolAddress), so
@@ -276,7 +283,7 @@ hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* ru
 #define HSVD_NOALLOC_MAX_K 64
 hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32_t m, int32_t n, int32_t k,
                                    int32_t power_iters, float* U, int64_t ldu, float* S, int32_t* rank,
-                                   void* stream);
+                                   int32_t* flags, void* stream);
 
 /* hsvd_destroy -- free everything the plan owns; NULL is accepted. */
 void hsvd_destroy(hsvd_plan_t plan);

@@ -86,6 +86,14 @@ struct Tables {
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// The call's status words as the bit set of hsvd_block_svd_noalloc's flags
+// output (1 Jacobi sweep cap reached, 2 CholeskyQR dropped directions,
+// 4 non-finite values met).
+__global__ void k_noalloc_flags(const DevStatus* st, int32_t* flags) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *flags = (st->not_converged ? 1 : 0) | (st->chol_dropped ? 2 : 0) | (st->nonfinite ? 4 : 0);
+}
+
 GT gt_blank() {
   GT g;
   std::memset(&g, 0, sizeof(g));
@@ -107,7 +115,7 @@ std::vector<GemmItem> items_of(const GT& g) {
 
 extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32_t m, int32_t n, int32_t k,
                                               int32_t power_iters, float* U, int64_t ldu, float* S, int32_t* rank,
-                                              void* stream) {
+                                              int32_t* flags, void* stream) {
   using namespace hsvd;
   if (!A || !U || !S || !rank) return HSVD_EINVAL;
   if (m < 1 || n < 1 || k < 1 || lda < n || ldu < m || power_iters < 0 || power_iters > 8) return HSVD_EINVAL;
@@ -311,6 +319,10 @@ extern "C" hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32
   if (e == cudaSuccess) e = launch_rowmajor_to_colmajor<float>(Ub, k, m, rk, k, U, ldu, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S, sig, sizeof(float) * k, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(rank, rk, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && flags) {
+    k_noalloc_flags<<<1, 32, 0, s>>>(dst, flags);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return HSVD_ECUDA;

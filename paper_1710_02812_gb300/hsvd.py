@@ -100,7 +100,7 @@ def lib():
         L.hsvd_set_timing.restype = ctypes.c_int
         L.hsvd_step_times.argtypes = [P, ctypes.POINTER(dbl), i32, ctypes.POINTER(i32)]
         L.hsvd_step_times.restype = ctypes.c_int
-        L.hsvd_block_svd_noalloc.argtypes = [P, i64, i32, i32, i32, i32, P, i64, P, P, P]
+        L.hsvd_block_svd_noalloc.argtypes = [P, i64, i32, i32, i32, i32, P, i64, P, P, P, P]
         L.hsvd_block_svd_noalloc.restype = ctypes.c_int
         L.hsvd_last_error.argtypes = [P]
         L.hsvd_last_error.restype = ctypes.c_char_p
@@ -327,13 +327,55 @@ def hsvd_jacobi_pair(n: int, rnd: int, slot: int):
     return p.value, q.value
 
 
-def hsvd_block_svd_noalloc(A, m, n, k, power_iters, U, S, rank, stream=None, lda=None, ldu=None):
+def check_noalloc_args(A, m, n, k, U, S, rank, flags=None, lda=None, ldu=None, require_cuda=True) -> None:
+    """Arguments of hsvd_block_svd_noalloc, checked before the call: the C
+    side sees raw pointers and would read past A or write past U, S, rank or
+    flags if they were too small or of the wrong type.  A is a 2-D float32
+    (m, n) tensor with unit column stride and row stride >= n (or lda); U a
+    contiguous float32 tensor of at least k * ldu elements (column-major
+    m x k, ldu >= m); S float32 with at least k elements; rank and flags
+    int32 with at least one element.  require_cuda=False skips the device
+    check (the shape and type checks run without a GPU)."""
+    import torch
+    for name, t in (("A", A), ("U", U), ("S", S), ("rank", rank), ("flags", flags)):
+        if t is None and name == "flags":
+            continue
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: a torch tensor is required")
+        if require_cuda and not t.is_cuda:
+            raise ValueError(f"{name}: a CUDA tensor is required (the entry point reads and writes device memory)")
+    m, n, k = int(m), int(n), int(k)
+    if A.dim() != 2 or tuple(A.shape) != (m, n):
+        raise ValueError(f"A: shape {tuple(A.shape)}, expected {(m, n)}")
+    if A.dtype != torch.float32:
+        raise TypeError(f"A: dtype {A.dtype}, float32 required")
+    lda = A.stride(0) if lda is None else int(lda)
+    if (n > 1 and A.stride(1) != 1) or (m > 1 and A.stride(0) < n) or lda < n or (m > 1 and lda != A.stride(0)):
+        raise ValueError(f"A: rows must be contiguous with leading dimension >= n (strides {A.stride()}, lda {lda})")
+    ldu = m if ldu is None else int(ldu)
+    if ldu < m:
+        raise ValueError(f"ldu {ldu} < m {m}")
+    for name, t, dt, need in (("U", U, torch.float32, k * ldu), ("S", S, torch.float32, k),
+                              ("rank", rank, torch.int32, 1), ("flags", flags, torch.int32, 1)):
+        if t is None:
+            continue
+        if t.dtype != dt:
+            raise TypeError(f"{name}: dtype {t.dtype}, {dt} required")
+        if not t.is_contiguous() or t.numel() < need:
+            raise ValueError(f"{name}: a contiguous tensor of at least {need} elements is required")
+
+
+def hsvd_block_svd_noalloc(A, m, n, k, power_iters, U, S, rank, stream=None, lda=None, ldu=None, flags=None):
     """Rank-k SVD of one block with no device allocation: A (m x n, row
     major), U (column-major m x k storage, e.g. a k x m row-major tensor),
-    S (k) and rank (one int32) are CUDA tensors; returns the status code."""
+    S (k), rank (one int32) and, optionally, flags (one int32: 1 Jacobi not
+    converged, 2 CholeskyQR dropped directions, 4 non-finite values) are CUDA
+    tensors; returns the status code."""
+    check_noalloc_args(A, m, n, k, U, S, rank, flags, lda, ldu)
     return lib().hsvd_block_svd_noalloc(A.data_ptr(), lda if lda is not None else A.stride(0), m, n, k,
                                         power_iters, U.data_ptr(), ldu if ldu is not None else m, S.data_ptr(),
-                                        rank.data_ptr(), _stream_ptr(stream))
+                                        rank.data_ptr(), flags.data_ptr() if flags is not None else None,
+                                        _stream_ptr(stream))
 
 
 # ------------------------------------------------------------------ wrapper

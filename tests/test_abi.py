@@ -220,3 +220,47 @@ def test_gram_binding_rejects_mismatched_buffers():
         hsvd.hsvd_gram(x, torch.zeros(5, 5, dtype=torch.float64))
     with pytest.raises(ValueError, match="CUDA"):
         hsvd.hsvd_gram(x, torch.zeros(5, 5))
+
+
+def test_noalloc_binding_rejects_buffers_the_kernels_would_overrun():
+    """hsvd_block_svd_noalloc receives raw pointers: the binding checks every
+    buffer before the call (shape, type, strides, sizes, device)."""
+    import torch
+    m, n, k = 12, 10, 4
+
+    def args(**over):
+        a = dict(A=torch.zeros(m, n), m=m, n=n, k=k, U=torch.zeros(k, m), S=torch.zeros(k),
+                 rank=torch.zeros(1, dtype=torch.int32), flags=torch.zeros(1, dtype=torch.int32))
+        a.update(over)
+        return a
+
+    chk = hsvd.check_noalloc_args
+    chk(**args(), require_cuda=False)                                        # well-formed
+    chk(**args(flags=None), require_cuda=False)                              # flags are optional
+    chk(**args(A=torch.zeros(m, 16)[:, :n]), require_cuda=False)             # row stride 16 > n
+    with pytest.raises(ValueError, match="CUDA tensor"):                     # host memory
+        chk(**args())
+    with pytest.raises(ValueError, match="shape"):
+        chk(**args(A=torch.zeros(m + 1, n)), require_cuda=False)
+    with pytest.raises(TypeError, match="float32"):
+        chk(**args(A=torch.zeros(m, n, dtype=torch.float64)), require_cuda=False)
+    with pytest.raises(ValueError, match="contiguous"):
+        chk(**args(A=torch.zeros(n, m).t()), require_cuda=False)            # column stride != 1
+    with pytest.raises(ValueError, match="contiguous"):
+        chk(**args(lda=n - 1), require_cuda=False)
+    with pytest.raises(ValueError, match="at least 48"):
+        chk(**args(U=torch.zeros(k, m - 1)), require_cuda=False)             # fewer than k * ldu
+    with pytest.raises(ValueError, match="ldu"):
+        chk(**args(ldu=m - 1), require_cuda=False)
+    with pytest.raises(ValueError, match="at least 4"):
+        chk(**args(S=torch.zeros(k - 1)), require_cuda=False)
+    with pytest.raises(TypeError, match="int32"):
+        chk(**args(rank=torch.zeros(1, dtype=torch.int64)), require_cuda=False)
+    with pytest.raises(TypeError, match="int32"):
+        chk(**args(flags=torch.zeros(1)), require_cuda=False)
+    with pytest.raises(TypeError, match="torch tensor"):
+        chk(**args(S=[0.0] * k), require_cuda=False)
+    # the public entry point checks before any library call
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        hsvd.hsvd_block_svd_noalloc(torch.zeros(m, n), m, n, k, 1, torch.zeros(k, m), torch.zeros(k),
+                                    torch.zeros(1, dtype=torch.int32))
