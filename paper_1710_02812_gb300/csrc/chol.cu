@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "jacobi.cuh"
@@ -437,6 +438,309 @@ __global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict_
   }
 }
 
+// ------------------------------------------------------------------ wide FP32 Grams
+// Blocked Cholesky and blocked triangular inverse for FP32 Grams of 129..256
+// columns (one CTA of 512 threads per Gram).  The scaled Gram Gh = S G S
+// (unit diagonal) is factored as Gh = Rh^T Rh with relative pivot dropping;
+// R = Rh S^{-1} and R^{-1} = S Rh^{-1}.  Only the upper triangle is kept, as
+// 32 x 32 tiles (row stride 36 floats: 16-byte rows, and rows 0..7 of a tile
+// start in distinct bank groups) in shared memory, 36 tiles for k <= 256.
+//   factor, per block column J: one warp factors the diagonal tile (lane c
+//     keeps column c in registers, row j broadcast by shuffles); the panel
+//     Rh[J, C] = Rh[J, J]^{-T} Gh[J, C] by forward substitution (lane =
+//     column); the trailing tiles Gh[I, C] -= Rh[J, I]^T Rh[J, C], each a
+//     32 x 32 x 32 product with an 8 x 4 register tile per lane.
+//   inverse, bottom-up by block rows I: X[I, I] = Rh[I, I]^{-1} (one warp,
+//     back substitution, lane = column) while other warps form
+//     T_J = sum_{I < L <= J} Rh[I, L] X[L, J]; then X[I, J] = -X[I, I] T_J,
+//     written over Rh[I, J] (row block I of Rh is not read again).
+// Three CTA barriers per block column or block row instead of one per
+// column of the elimination.
+constexpr int CB_LD = 36;
+constexpr int CB_TS = 32 * CB_LD;
+constexpr int CB_NT = 8;
+constexpr int CB_NUP = CB_NT * (CB_NT + 1) / 2;
+constexpr int CB_THREADS = 256;
+constexpr int CB_NW = CB_THREADS / 32;
+constexpr size_t CB_SMEM = (size_t)(CB_NUP + CB_NT + 1) * CB_TS * sizeof(float);
+
+__device__ __forceinline__ int cb_tile(int I, int J, int nt) { return I * nt - I * (I - 1) / 2 + (J - I); }
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<float>* __restrict__ tasks,
+                                                            DevStatus* __restrict__ st, float tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* __restrict__ tiles = reinterpret_cast<float*>(smem_raw);
+  float* __restrict__ temps = tiles + CB_NUP * CB_TS;
+  float* __restrict__ xdiag = temps + CB_NT * CB_TS;
+  __shared__ float sc[32 * CB_NT];
+  __shared__ int bad, ndrop;
+  const CholTask<float>& tk = tasks[blockIdx.x];
+  const int k = eff(tk.k);
+  if (k <= 0) return;
+  const int nt = (k + 31) >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
+
+  if (tid == 0) {
+    bad = 0;
+    ndrop = 0;
+  }
+  __syncthreads();
+  for (int j = tid; j < 32 * nt; j += CB_THREADS) {
+    float s = 0.f;
+    if (j < k) {
+      const float g = tk.G[(int64_t)j * tk.ldg + j];
+      if (!isfinite(g)) bad = 1;
+      s = (g > 0.f && isfinite(g)) ? 1.f / sqrtf(g) : 0.f;
+    }
+    sc[j] = s;
+  }
+  __syncthreads();
+  if (tid == 0 && bad && st) atomicAdd(&st->nonfinite, 1);
+  // scaled upper triangle, tile (I, J) entry (r, c) = Gh[32 I + r][32 J + c]
+  {
+    int t = 0;
+    for (int I = 0; I < nt; ++I)
+      for (int J = I; J < nt; ++J, ++t) {
+        if (t % CB_NW != warp) continue;
+        float* T = tiles + t * CB_TS;
+        const int c = 32 * J + lane;
+        for (int r = 0; r < 32; ++r) {
+          const int i = 32 * I + r;
+          float v = 0.f;
+          if (i < k && c < k && c >= i) v = tk.G[(int64_t)i * tk.ldg + c] * sc[i] * sc[c];
+          T[r * CB_LD + lane] = v;
+        }
+      }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- factor
+  for (int J = 0; J < nt; ++J) {
+    float* D = tiles + cb_tile(J, J, nt) * CB_TS;
+    if (warp == 0) {
+      float col[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) col[r] = D[r * CB_LD + lane];
+      int nd = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float d = __shfl_sync(FULL, col[j], j);
+        const int gj = 32 * J + j;
+        const bool pad = gj >= k;
+        const bool drop = pad || !(sc[gj] > 0.f) || !(d > tau);
+        if (drop && !pad) ++nd;
+        const float rinv = drop ? 0.f : 1.f / sqrtf(d);
+        const float rj = lane >= j ? col[j] * rinv : 0.f;
+        col[j] = rj;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) {
+          if (i > j) {  // resolved at compile time: both loops are unrolled
+            const float ri = __shfl_sync(FULL, rj, i);
+            if (lane >= i) col[i] = fmaf(-ri, rj, col[i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) D[r * CB_LD + lane] = lane >= r ? col[r] : 0.f;
+      if (lane == 0 && nd) ndrop += nd;
+    }
+    __syncthreads();
+    // panel: solve Rh[J,J]^T X = Gh[J, C] for every C > J (lane = column)
+    for (int C = J + 1 + warp; C < nt; C += CB_NW) {
+      float* B = tiles + cb_tile(J, C, nt) * CB_TS;
+      float x[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) x[r] = B[r * CB_LD + lane];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        float acc = x[r];
+#pragma unroll
+        for (int l = 0; l < r; ++l) acc = fmaf(-D[l * CB_LD + r], x[l], acc);
+        const float drr = D[r * CB_LD + r];
+        x[r] = drr > 0.f ? acc / drr : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) B[r * CB_LD + lane] = x[r];
+    }
+    __syncthreads();
+    // trailing update: Gh[I, C] -= Rh[J, I]^T Rh[J, C], J < I <= C
+    {
+      const int m = nt - J - 1;
+      const int ntask = m * (m + 1) / 2;
+      const int ri = lane >> 3, ci = lane & 7;
+      for (int task = warp; task < ntask; task += CB_NW) {
+        int I = J + 1, rem = task;
+        while (rem >= nt - I) {
+          rem -= nt - I;
+          ++I;
+        }
+        const int C = I + rem;
+        const float* A = tiles + cb_tile(J, I, nt) * CB_TS;
+        const float* Bt = tiles + cb_tile(J, C, nt) * CB_TS;
+        float* O = tiles + cb_tile(I, C, nt) * CB_TS;
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          const float4 a0 = ld4(A + l * CB_LD + ri * 8), a1 = ld4(A + l * CB_LD + ri * 8 + 4);
+          const float4 b = ld4(Bt + l * CB_LD + ci * 4);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float4* o = reinterpret_cast<float4*>(O + (ri * 8 + u) * CB_LD + ci * 4);
+          float4 w = *o;
+          w.x -= acc[u][0];
+          w.y -= acc[u][1];
+          w.z -= acc[u][2];
+          w.w -= acc[u][3];
+          *o = w;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && ndrop > 0 && st) atomicAdd(&st->chol_dropped, ndrop);
+
+  // R[i][c] = Rh[i][c] / s_c (c >= i)
+  if (tk.R) {
+    for (int i = warp; i < k; i += CB_NW)
+      for (int c = lane; c < k; c += 32) {
+        float v = 0.f;
+        if (c >= i && sc[c] > 0.f) v = tiles[cb_tile(i >> 5, c >> 5, nt) * CB_TS + (i & 31) * CB_LD + (c & 31)] / sc[c];
+        tk.R[(int64_t)i * tk.ldr + c] = v;
+      }
+  }
+  if (!tk.Rinv) return;
+
+  // ---------------------------------------------------------------- inverse
+  for (int I = nt - 1; I >= 0; --I) {
+    const float* D = tiles + cb_tile(I, I, nt) * CB_TS;
+    if (warp == 0) {
+      // X[I, I] = D^{-1}: column c by back substitution
+      float x[32];
+      const float dcc = D[lane * CB_LD + lane];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) x[r] = 0.f;
+#pragma unroll
+      for (int r = 31; r >= 0; --r) {
+        float acc = r == lane ? 1.f : 0.f;
+#pragma unroll
+        for (int l = r + 1; l < 32; ++l) acc = fmaf(-D[r * CB_LD + l], x[l], acc);
+        const float drr = D[r * CB_LD + r];
+        x[r] = (r <= lane && drr > 0.f && dcc > 0.f) ? acc / drr : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) xdiag[r * CB_LD + lane] = x[r];
+    } else {
+      // T_J = sum_{I < L <= J} Rh[I, L] X[L, J]: task (J, half h), 16 rows
+      // 16 h + ri + 4 u (u < 4) and columns 4 ci .. 4 ci + 3 per lane
+      const int ri = lane >> 3, ci = lane & 7;
+      const int ntask = 2 * (nt - 1 - I);
+      for (int task = warp - 1; task < ntask; task += CB_NW - 1) {
+        const int J = I + 1 + (task >> 1), h = task & 1;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        for (int L = I + 1; L <= J; ++L) {
+          const float* A = tiles + cb_tile(I, L, nt) * CB_TS;
+          const float* Bt = tiles + cb_tile(L, J, nt) * CB_TS;
+#pragma unroll 2
+          for (int l = 0; l < 32; l += 4) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = ld4(A + (16 * h + ri + 4 * u) * CB_LD + l);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = ld4(Bt + (l + q) * CB_LD + ci * 4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float av[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                acc[u][0] = fmaf(av[q], b[q].x, acc[u][0]);
+                acc[u][1] = fmaf(av[q], b[q].y, acc[u][1]);
+                acc[u][2] = fmaf(av[q], b[q].z, acc[u][2]);
+                acc[u][3] = fmaf(av[q], b[q].w, acc[u][3]);
+              }
+            }
+          }
+        }
+        float* T = temps + (J - I - 1) * CB_TS;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<float4*>(T + (16 * h + ri + 4 * u) * CB_LD + ci * 4) =
+              make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+      }
+    }
+    __syncthreads();
+    // X[I, J] = -X[I, I] T_J over Rh[I, J]; X[I, I] copied over Rh[I, I].
+    // Rows ri + 4 u (u < 8) and columns 4 ci .. 4 ci + 3 per lane.
+    {
+      const int ri = lane >> 3, ci = lane & 7;
+      for (int J = I + warp; J < nt; J += CB_NW) {
+        float* O = tiles + cb_tile(I, J, nt) * CB_TS;
+        if (J == I) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int r = ri + 4 * u;
+            *reinterpret_cast<float4*>(O + r * CB_LD + ci * 4) = ld4(xdiag + r * CB_LD + ci * 4);
+          }
+          continue;
+        }
+        const float* T = temps + (J - I - 1) * CB_TS;
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 2
+        for (int mm = 0; mm < 32; mm += 4) {
+          float4 b[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) b[q] = ld4(T + (mm + q) * CB_LD + ci * 4);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 a = ld4(xdiag + (ri + 4 * u) * CB_LD + mm);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[u][0] = fmaf(av[q], b[q].x, acc[u][0]);
+              acc[u][1] = fmaf(av[q], b[q].y, acc[u][1]);
+              acc[u][2] = fmaf(av[q], b[q].z, acc[u][2]);
+              acc[u][3] = fmaf(av[q], b[q].w, acc[u][3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          *reinterpret_cast<float4*>(O + (ri + 4 * u) * CB_LD + ci * 4) =
+              make_float4(-acc[u][0], -acc[u][1], -acc[u][2], -acc[u][3]);
+      }
+    }
+    __syncthreads();
+  }
+  // R^{-1}[l][j] = s_l X[l][j] (l <= j)
+  for (int l = warp; l < k; l += CB_NW)
+    for (int j = lane; j < k; j += 32) {
+      float v = 0.f;
+      if (j >= l) v = sc[l] * tiles[cb_tile(l >> 5, j >> 5, nt) * CB_TS + (l & 31) * CB_LD + (j & 31)];
+      tk.Rinv[(int64_t)l * tk.ldri + j] = v;
+    }
+}
+
 }  // namespace
 
 template <class T>
@@ -444,6 +748,13 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
                         cudaStream_t s, bool with_product) {
   if (ntasks <= 0) return cudaSuccess;
   if (kcap > 256) return cudaErrorInvalidValue;
+  if (std::is_same<T, float>::value && kcap > 128 && !with_product) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CB_SMEM);
+    if (e != cudaSuccess) return e;
+    k_chol_wide<<<ntasks, CB_THREADS, CB_SMEM, s>>>(reinterpret_cast<const CholTask<float>*>(tasks), st,
+                                                   (float)tau);
+    return cudaGetLastError();
+  }
   {
     const int kb = kcap <= 32 ? 2 : kcap <= 64 ? 4 : kcap <= 128 ? 8 : 16;
     // shared memory only for staging R2 and R1 of the CholeskyQR2 product
@@ -492,7 +803,9 @@ cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatu
   return cudaGetLastError();
 }
 
-bool chol_uses_smem(int kcap, size_t elem) { return (size_t)kcap * kcap * elem <= 200 * 1024; }
+bool chol_uses_smem(int kcap, size_t elem) {
+  return (size_t)kcap * kcap * elem <= 200 * 1024 || (elem == 4 && kcap <= 256);
+}
 
 template cudaError_t launch_chol<float>(const CholTask<float>*, int, int, DevStatus*, double, cudaStream_t, bool);
 template cudaError_t launch_chol<double>(const CholTask<double>*, int, int, DevStatus*, double, cudaStream_t,

@@ -575,15 +575,18 @@ struct Builder {
       k.K = K;
       k.D = reinterpret_cast<float*>(o.C);
       k.ldd = o.ldc;
-      // Long K is split into chunks of at most 16 K tiles (1024), at most 16
-      // chunks, summed afterwards in FP32: the tensor cores' FP32
-      // accumulation drifts toward zero with the number of accumulation steps
-      // (relative ~1.5e-5 over K = 8192 in one accumulator), and the chunks
-      // also give short, wide products more CTAs.
+      // Long K is split into chunks of at most 16 K tiles (1024), summed
+      // afterwards in FP32: the tensor cores' FP32 accumulation drifts toward
+      // zero with the number of accumulation steps (relative ~1.5e-5 over
+      // K = 8192 in one accumulator, ~1.5e-5 over K = 65536 in chunks of
+      // 4096), and the chunks also give short, wide products more CTAs.  The
+      // partial tiles are capped at 4 GB per product (longer chunks beyond).
       const int ktiles = (K + 63) / 64;
       int nkc = 1;
       if (ktiles > 32) {
-        nkc = std::min(16, (ktiles + 15) / 16);
+        const int64_t per_chunk = (int64_t)M * (((o.N.cap + 3) / 4) * 4) * 4;
+        const int cap = (int)std::max<int64_t>(16, std::min<int64_t>(256, (int64_t(4) << 30) / per_chunk));
+        nkc = std::min(cap, (ktiles + 15) / 16);
         k.kchunk_tiles = (ktiles + nkc - 1) / nkc;
         nkc = (ktiles + k.kchunk_tiles - 1) / k.kchunk_tiles;
         k.ldp = ((o.N.cap + 3) / 4) * 4;
