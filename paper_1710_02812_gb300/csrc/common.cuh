@@ -270,6 +270,8 @@ size_t jacobi_cluster_smem(int nrcap, int nccap, bool want_v, int C);
 cudaError_t launch_jacobi_cluster(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                                   int C, TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 // The FP32 block-pair core kernel (up to 128 x 128; *done false: not launched).
+cudaError_t launch_jacobi_split(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                                TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                              TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem);

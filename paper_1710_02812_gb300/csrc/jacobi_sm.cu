@@ -4,7 +4,7 @@
 // final projection core.  k_jacobi keeps the working copy in shared or global
 // memory; k_jacobi_sm is the shared-memory specialisation.  launch_jacobi
 // dispatches every core launch of the path: the FP32 block-pair kernel, the
-// cluster kernel, then these.
+// column-split and row-split cluster kernels, then these.
 #include <math.h>
 
 #include <cstdlib>
@@ -579,7 +579,10 @@ cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int
   if constexpr (sizeof(T) == 4) {
     e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
     if (e != cudaSuccess || done) return e;
-    // Cores one CTA cannot hold are spread over a cluster.
+    // Cores one CTA cannot hold are spread over a cluster: by columns (two
+    // CTAs, columns exchanged twice per sweep), else by rows.
+    e = launch_jacobi_split(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
+    if (e != cudaSuccess || done) return e;
     const int C = jacobi_cluster_size(ntasks, nrcap, nccap, !jacobi_sm_fits(nrcap, nccap, want_v, sizeof(T)));
     if (C >= 2) {
       e = launch_jacobi_cluster(tasks, ntasks, nrcap, nccap, want_v, C, tp, st, s, &done);
