@@ -97,6 +97,9 @@ typedef struct {
   uint64_t seed;        /* seed of the block sketch matrix (default 0x1710028) */
   int32_t max_sweeps;   /* one-sided Jacobi sweep cap (default 40) */
   int32_t host_staging; /* nonzero: reserve device staging for hsvd_run_host */
+  int32_t stop_after_rows; /* nonzero: a band plan (one matrix, COL_THEN_ROW): hsvd_run
+                              stops after the row MAT tree, whose result hsvd_tree_root
+                              returns; U is recovered with the hsvd_recover_* stages */
 } hsvd_options;
 
 /* Device status words, read back by hsvd_status_query. */
@@ -284,6 +287,80 @@ hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* ru
 hsvd_status hsvd_block_svd_noalloc(const float* A, int64_t lda, int32_t m, int32_t n, int32_t k,
                                    int32_t power_iters, float* U, int64_t ldu, float* S, int32_t* rank,
                                    int32_t* flags, void* stream);
+
+/* ---- one matrix split over several GPUs by row bands ----
+ * The blocks of a row slab, its column MAT tree and its slab step involve no
+ * other slab, and the row MAT tree only meets other slabs at its merges
+ * (Section 3.1: the block SVDs and the merges of a level are independent).
+ * A matrix whose row slabs are shared out over ranks (contiguous bands of
+ * whole slabs) is therefore factored as:
+ *   1. every rank: a band plan (hsvd_plan with opts->stop_after_rows) run on
+ *      its band gives the root of its own row tree (hsvd_tree_root);
+ *   2. the roots are merged along a binary tree over the ranks (rank r takes
+ *      rank r + 2^l's root at level l when r is a multiple of 2^(l+1); with
+ *      2^L slabs per rank this is the paper's tree): hsvd_merge_plan /
+ *      hsvd_merge_run on the receiving rank;
+ *   3. V_hat (the last root) is sent to every rank, and U is recovered from
+ *      SVD(X V_hat) with CholeskyQR2 over the bands (hsvd_recover_*): each
+ *      stage leaves a small array whose sum (or max / min) over the ranks is
+ *      the next stage's input.
+ * The exchanges between stages are the caller's (e.g. NCCL): the library
+ * computes, the caller moves n x rank_cap factors and rank_cap^2 Grams. */
+
+/* hsvd_tree_root -- the row MAT tree's result for matrix idx of the last run
+ * (or the merge of the last hsvd_merge_run of a merge plan): V_hat, n x
+ * rank_cap column-major into device V (ldv >= n; columns past the rank are
+ * zero), its singular values into device S (rank_cap values, zero past the
+ * rank) and the rank into host *rank (the call then synchronises stream).
+ * Any output may be NULL.  EINVAL, ENOTREADY (no run yet), ECUDA. */
+hsvd_status hsvd_tree_root(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* V, int64_t ldv, void* S,
+                           void* stream);
+
+/* hsvd_merge_plan -- a plan holding one MAT merge (Section 3, Eqs.
+ * orthmerge1 / orthmerge) of two factor pairs of height h: the merge of two
+ * ranks' row-tree roots.  mode, param, rank_cap and prec as for the band
+ * plans (BF16_MIXED merges in FP32; F64 in FP64); opts may be NULL (its
+ * rank_tol and max_sweeps are used).  EINVAL, ENOMEM, ECUDA. */
+hsvd_status hsvd_merge_plan(hsvd_plan_t* out, int64_t h, int32_t rank_cap, hsvd_trunc mode, double param,
+                            hsvd_prec prec, const hsvd_options* opts);
+
+/* hsvd_merge_run -- merge (V1, S1) of rank r1 with (V2, S2) of rank r2:
+ * device column-major h x rank_cap factors (ld >= h) and device singular
+ * values (at least r values), host ranks 0..rank_cap; the result (V S
+ * truncated by the plan's rule) through hsvd_tree_root(plan, 0, ...).
+ * Asynchronous on stream.  EINVAL (not a merge plan, bad sizes), ECUDA. */
+hsvd_status hsvd_merge_run(hsvd_plan_t plan, const void* V1, int64_t ld1, const void* S1, int32_t r1,
+                           const void* V2, int64_t ld2, const void* S2, int32_t r2, void* stream);
+
+/* Left-vector recovery of a band plan's rows (Section 3: SVD(X V_hat) =
+ * U_y S_y V_y^T, U = U_y, V = V_hat V_y), CholeskyQR2 of Y = X V_hat with
+ * its Grams summed over the bands.  Arrays are device, of the factor type
+ * (double for F64, float otherwise) unless stated; Grams are rank_cap x
+ * rank_cap row-major and only their upper triangles are meaningful.  Each
+ * stage is asynchronous on stream and requires the previous one (else
+ * ENOTREADY); the input of a band is the last run's.
+ *   hsvd_recover_begin:  V_hat (n x rank_cap column-major, ldv >= n) of rank r;
+ *                        Y = X_band V_hat, G = Y^T Y.
+ *   hsvd_recover_orth:   Gsum = sum of G over the bands; R1 = chol(Gsum),
+ *                        Q = Y R1^-1, G2 = Q^T Q.
+ *   hsvd_recover_core:   G2sum = sum of G2; R2, Q <- Q R2^-1, R = R2 R1,
+ *                        R = A S W^T (one-sided Jacobi), U = Q A (this band's
+ *                        rows), V = V_hat W; absmax[c] = max over the band's
+ *                        rows of |U[i][c]| (rank_cap values).
+ *   hsvd_recover_signs:  absmax_all = the maximum of absmax over the bands;
+ *                        row0 = the band's first row in the matrix;
+ *                        key[c] (int64) = 2 (row0 + i) + (U[i][c] < 0) for the
+ *                        band's first row i with |U[i][c]| = absmax_all[c],
+ *                        else INT64_MAX.
+ *   hsvd_recover_finish: key_min = the minimum of key over the bands: the
+ *                        largest-magnitude entry of each U column (the first
+ *                        on ties) is made positive, V following.
+ * Then hsvd_factors(plan, 0, ...) gives this band's rows of U, S and V. */
+hsvd_status hsvd_recover_begin(hsvd_plan_t plan, const void* Vhat, int64_t ldv, int32_t r, void* G, void* stream);
+hsvd_status hsvd_recover_orth(hsvd_plan_t plan, const void* Gsum, void* G2, void* stream);
+hsvd_status hsvd_recover_core(hsvd_plan_t plan, const void* G2sum, void* absmax, void* stream);
+hsvd_status hsvd_recover_signs(hsvd_plan_t plan, const void* absmax_all, int64_t row0, int64_t* key, void* stream);
+hsvd_status hsvd_recover_finish(hsvd_plan_t plan, const int64_t* key_min, void* stream);
 
 /* hsvd_destroy -- free everything the plan owns; NULL is accepted. */
 void hsvd_destroy(hsvd_plan_t plan);

@@ -70,6 +70,11 @@ struct GemmTask {
   int kchunk;   // TN split-K: rows of K per chunk (0 = whole K)
   int nkc;      // number of K chunks
   int mtiles, ntiles;
+  // Structure the kernels may exploit (results are the same without it):
+  // sym: C = A^T A is symmetric and only its upper triangle is read, so
+  // output tiles strictly below the diagonal are not computed; btri: B is
+  // upper triangular, so output column n needs only K rows 0..n.
+  int sym, btri;
 };
 
 // Work item of a tiled GEMM launch: (task, tile row, tile column, K chunk).
@@ -270,6 +275,21 @@ size_t jacobi_cluster_smem(int nrcap, int nccap, bool want_v, int C);
 cudaError_t launch_jacobi_cluster(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                                   int C, TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 // The FP32 block-pair core kernel (up to 128 x 128; *done false: not launched).
+// row split across ranks (small.cu)
+template <class T>
+cudaError_t launch_colmajor_to_rowmajor(const T* src, int64_t lds, int rows, int r, int kcap, T* dst, cudaStream_t s);
+template <class T>
+cudaError_t launch_rowmajor_to_colmajor_full(const T* src, int64_t lds, int rows, const int* rank, int kcap, T* dst,
+                                             int64_t ldd, cudaStream_t s);
+cudaError_t launch_set_words(int* p, int v, long long* q, long long w, cudaStream_t s);
+template <class T>
+cudaError_t launch_band_absmax(const T* U, int64_t ldu, int rows, const int* rank, int kcap, T* amax, cudaStream_t s);
+template <class T>
+cudaError_t launch_band_keys(const T* U, int64_t ldu, int rows, const int* rank, int kcap, const T* amax_all,
+                             const long long* row0, long long* key, cudaStream_t s);
+template <class T>
+cudaError_t launch_band_flip(T* U, int64_t ldu, int rows, T* V, int64_t ldv, int vrows, const int* rank, int kcap,
+                             const long long* key, cudaStream_t s);
 cudaError_t launch_jacobi_split(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                                 TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,

@@ -283,6 +283,9 @@ __global__ void __launch_bounds__(256) k_gemm2(const GemmTask<TA, float, float>*
     kb = it.kc * tk.kchunk;
     ke = min(Kt, kb + tk.kchunk);
   }
+  // B upper triangular: column n of the tile needs rows k <= n only (an
+  // empty range leaves a zero partial tile)
+  if (!IS_TN && tk.btri && K2 == 0) ke = min(ke, n0 + BN2);
   const TA* A = tk.A;
   int64_t lda = tk.lda;
   if (tk.mat >= 0) {

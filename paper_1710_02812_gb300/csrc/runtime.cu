@@ -138,6 +138,36 @@ struct PlanImpl {
   bool graph_off = false;
   size_t graph_from = 0;  // first step inside the graph
 
+  // One matrix split over ranks by row bands: a band plan stops after the
+  // row MAT tree (stop_rows) and recovers U in stages whose sums over the
+  // bands the caller makes between them; a merge plan holds one MAT merge of
+  // two factors (merge_only).
+  bool stop_rows = false;
+  bool merge_only = false;
+  struct Root {
+    void* V = nullptr;  // h x kcap row-major
+    void* sig = nullptr;
+    int* rank = nullptr;
+    int h = 0;
+  };
+  std::vector<Root> roots;        // per matrix: the row tree's result (merge plan: the merge)
+  std::vector<Step> stage_steps[5];
+  struct Band {
+    void* vin = nullptr;  // V_hat, n x kcap row-major
+    int* rin = nullptr;
+    void* G1 = nullptr;
+    void* G2 = nullptr;
+    void* amax = nullptr;
+    long long* key = nullptr;
+    long long* row0 = nullptr;
+  } band;
+  struct MergeIn {
+    void* V[2] = {nullptr, nullptr};
+    void* sig[2] = {nullptr, nullptr};
+    int* rank[2] = {nullptr, nullptr};
+  } min_;
+  int stage_next = -1;  // next recovery stage of a band plan (-1: none run yet)
+
   ~PlanImpl() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (graph) cudaGraphDestroy(graph);
@@ -301,6 +331,13 @@ struct Builder {
     return g;
   }
 
+  // An output tile of a symmetric product lying strictly below the diagonal.
+  template <class G>
+  static bool below_diag(const G& g, int mt, int nt) {
+    constexpr int TM = gemm_tile_m(sizeof(T)), TN = GEMM_TILE_N;
+    return g.sym && (nt + 1) * TN <= mt * TM;
+  }
+
   template <class G>
   void finish_items(std::vector<G>& tasks, bool is_tn, std::vector<GemmItem>& items, std::vector<GemmItem>& red) {
     constexpr int TM = gemm_tile_m(sizeof(T)), TN = GEMM_TILE_N;
@@ -331,11 +368,13 @@ struct Builder {
         const int parts = sizeof(T) == 4 ? GEMM_REDUCE_PARTS : 1;  // FP64 reduces a tile per CTA
         for (int mt = 0; mt < g.mtiles; ++mt)
           for (int nt = 0; nt < g.ntiles; ++nt)
-            for (int q = 0; q < parts; ++q) red.push_back(GemmItem{(int)t, mt, nt, q});
+            if (!below_diag(g, mt, nt))
+              for (int q = 0; q < parts; ++q) red.push_back(GemmItem{(int)t, mt, nt, q});
       }
       for (int kc = 0; kc < g.nkc; ++kc)
         for (int mt = 0; mt < g.mtiles; ++mt)
-          for (int nt = 0; nt < g.ntiles; ++nt) items.push_back(GemmItem{(int)t, mt, nt, kc});
+          for (int nt = 0; nt < g.ntiles; ++nt)
+            if (!below_diag(g, mt, nt)) items.push_back(GemmItem{(int)t, mt, nt, kc});
     }
   }
 
@@ -742,6 +781,7 @@ struct Builder {
         const T* in = pass == 0 ? w.A : w.tmp;
         const int64_t ldin = pass == 0 ? w.lda : w.kl;
         gram.push_back(tn(in, ldin, w.h, w.k, in, ldin, w.k, w.G, w.kl));
+        gram.back().sym = 1;  // the factorisation reads the upper triangle only
         CholTask<T> c;
         std::memset(&c, 0, sizeof(c));
         c.G = w.G;
@@ -769,7 +809,10 @@ struct Builder {
         }
         ch.push_back(c);
         T* out = last ? w.Q : w.tmp;
-        if (out) mult.push_back(nn(in, ldin, w.h, w.k, w.Rinv, w.kl, w.k, out, w.kl));
+        if (out) {
+          mult.push_back(nn(in, ldin, w.h, w.k, w.Rinv, w.kl, w.k, out, w.kl));
+          mult.back().btri = 1;  // R^{-1} is upper triangular
+        }
       }
       const std::string tag = name + ".p" + std::to_string(pass + 1);
       emit_gemm(tag + ".gram", gram, true);
@@ -911,7 +954,161 @@ struct Builder {
     return roots;
   }
 
+  // A merge plan: two input factors of height h (written by hsvd_merge_run)
+  // and one MAT merge (Section 3, Eq. orthmerge1) into the root.
+  void build_merge() {
+    const int h = (int)P.m[0];
+    Factor f1 = new_factor(h), f2 = new_factor(h);
+    if (base_real()) {
+      P.min_.V[0] = f1.U;
+      P.min_.sig[0] = f1.sig;
+      P.min_.rank[0] = f1.rank;
+      P.min_.V[1] = f2.U;
+      P.min_.sig[1] = f2.sig;
+      P.min_.rank[1] = f2.rank;
+    }
+    std::vector<Factor> outs;
+    auto ms = make_merges({{f1, f2}}, outs);
+    emit_merge_level("merge", ms);
+    P.roots.push_back(PlanImpl::Root{outs[0].U, outs[0].sig, outs[0].rank, h});
+    P.outs.assign(1, ProblemOut());
+  }
+
+  // Left-vector recovery of one row band (Section 3, projection paragraph:
+  // SVD(X V_hat)) split into stages around the sums over bands:
+  //   0: Y = X_band V_hat, G1 = Y^T Y
+  //   1: (G1 summed) R1, R1^-1 = chol(G1); Q1 = Y R1^-1; G2 = Q1^T Q1
+  //   2: (G2 summed) R2, R2^-1; Q2 = Q1 R2^-1; R = R2 R1; R = A S W^T;
+  //      U = Q2 A (this band's rows), V = V_hat W; per-column max |U|
+  //   3: (maxima over bands) keys of the first largest-magnitude entries
+  //   4: (smallest key over bands) signs: that entry made positive
+  void build_band_recovery() {
+    const int kc = P.kcap;
+    const int mm = (int)P.m[0], nn = (int)P.n[0];
+    T* Vin = alloc<T>((size_t)nn * kc);
+    int* rin = alloc<int>(1);
+    T* Y = alloc<T>((size_t)mm * kc);
+    T* G1 = alloc<T>((size_t)kc * kc);
+    T* R1 = alloc<T>((size_t)kc * kc);
+    T* R1i = alloc<T>((size_t)kc * kc);
+    T* Q1 = alloc<T>((size_t)mm * kc);
+    T* G2 = alloc<T>((size_t)kc * kc);
+    T* R2 = alloc<T>((size_t)kc * kc);
+    T* R2i = alloc<T>((size_t)kc * kc);
+    T* Q2 = alloc<T>((size_t)mm * kc);
+    T* R = alloc<T>((size_t)kc * kc);
+    T* A = alloc<T>((size_t)kc * kc);
+    T* Wm = alloc<T>((size_t)kc * kc);
+    T* Uf = alloc<T>((size_t)mm * kc);
+    T* Vf = alloc<T>((size_t)nn * kc);
+    T* sf = alloc<T>(kc);
+    int* rf = alloc<int>(1);
+    T* amax = alloc<T>(kc);
+    long long* key = alloc<long long>(kc);
+    long long* row0 = alloc<long long>(1);
+    if (base_real()) {
+      P.band.vin = Vin;
+      P.band.rin = rin;
+      P.band.G1 = G1;
+      P.band.G2 = G2;
+      P.band.amax = amax;
+      P.band.key = key;
+      P.band.row0 = row0;
+    }
+    ProblemOut& po = P.outs[0];
+    po.mm = mm;
+    po.nn = nn;
+    po.trans = false;
+    po.U = Uf;
+    po.V = Vf;
+    po.sig = sf;
+    po.rank = rf;
+    const Dim kv = dimd(kc, rin);
+    auto into = [&](int stage, auto&& fn) {
+      std::swap(P.steps, P.stage_steps[stage]);
+      fn();
+      std::swap(P.steps, P.stage_steps[stage]);
+    };
+    into(0, [&] {
+      std::vector<InputOp> ops{input_op(false, 0, false, 0, 0, mm, nn, Vin, kc, kv, Y, kc)};
+      emit_input("band.project", ops, true);
+      GS g = tn(Y, kc, mm, kv, Y, kc, kv, G1, kc);
+      g.sym = 1;
+      emit_gemm("band.gram1", std::vector<GS>{g}, true);
+    });
+    auto chol_task = [&](T* G, T* Rout, T* Rinv) {
+      CholTask<T> c;
+      std::memset(&c, 0, sizeof(c));
+      c.G = G;
+      c.ldg = kc;
+      c.k = kv;
+      c.R = Rout;
+      c.ldr = kc;
+      c.Rinv = Rinv;
+      c.ldri = kc;
+      return c;
+    };
+    into(1, [&] {
+      emit_chol("band.chol1", std::vector<CholTask<T>>{chol_task(G1, R1, R1i)}, kc);
+      GS m1 = nn_(Y, kc, mm, kv, R1i, kc, kv, Q1, kc);
+      m1.btri = 1;
+      emit_gemm("band.mul1", std::vector<GS>{m1}, false);
+      GS g2 = tn(Q1, kc, mm, kv, Q1, kc, kv, G2, kc);
+      g2.sym = 1;
+      emit_gemm("band.gram2", std::vector<GS>{g2}, true);
+    });
+    into(2, [&] {
+      emit_chol("band.chol2", std::vector<CholTask<T>>{chol_task(G2, R2, R2i)}, kc);
+      GS m2 = nn_(Q1, kc, mm, kv, R2i, kc, kv, Q2, kc);
+      m2.btri = 1;
+      emit_gemm("band.mul2", std::vector<GS>{m2}, false);
+      GS rp = nn_(R2, kc, kc, kv, R1, kc, kv, R, kc);
+      rp.M = kv;
+      emit_gemm("band.R", std::vector<GS>{rp}, false);
+      TruncParams tpf = tparams();
+      tpf.mode = 0;
+      tpf.param = kc;
+      JacobiTask<T> jj = jblank();
+      jj.load = 0;
+      jj.src = R;
+      jj.rs = kc;
+      jj.cs = 1;
+      jj.nr = kv;
+      jj.nc = kv;
+      jj.U = A;
+      jj.ldu = kc;
+      jj.ucap = kc;
+      jj.V = Wm;
+      jj.ldv = kc;
+      jj.sig = sf;
+      jj.rank = rf;
+      emit_jacobi("band.core", std::vector<JacobiTask<T>>{jj}, kc, kc, true, tpf);
+      emit_gemm("band.U", std::vector<GS>{nn_(Q2, kc, mm, kv, A, kc, dimd(kc, rf), Uf, kc)}, false);
+      emit_gemm("band.V", std::vector<GS>{nn_(Vin, kc, nn, kv, Wm, kc, dimd(kc, rf), Vf, kc)}, false);
+      P.steps.push_back(Step{"band.absmax", [Uf, mm, rf, kc, amax](cudaStream_t s) {
+                               return launch_band_absmax<T>(Uf, kc, mm, rf, kc, amax, s);
+                             }});
+      tag(7, 1, kc, 0, (double)mm * kc * sizeof(T));
+    });
+    into(3, [&] {
+      P.steps.push_back(Step{"band.keys", [Uf, mm, rf, kc, amax, row0, key](cudaStream_t s) {
+                               return launch_band_keys<T>(Uf, kc, mm, rf, kc, amax, row0, key, s);
+                             }});
+      tag(7, 1, kc, 0, (double)mm * kc * sizeof(T));
+    });
+    into(4, [&] {
+      P.steps.push_back(Step{"band.signs", [Uf, Vf, mm, nn, rf, kc, key](cudaStream_t s) {
+                               return launch_band_flip<T>(Uf, kc, mm, Vf, kc, nn, rf, kc, key, s);
+                             }});
+      tag(7, 1, kc, 0, (double)(mm + nn) * kc * sizeof(T));
+    });
+  }
+
   void build() {
+    if (P.merge_only) {
+      build_merge();
+      return;
+    }
     const int kc = P.kcap, kp = P.kp;
     const bool vt = P.tree == HSVD_TREE_ROW_THEN_COL;
     const int64_t brr = vt ? P.bc : P.br;
@@ -1145,6 +1342,12 @@ struct Builder {
 
     // ---------------------------------------------------- row MAT trees
     std::vector<Factor> vhat = tree("rowmerge", row_lists);
+    for (int b = 0; b < P.batch; ++b)
+      P.roots.push_back(PlanImpl::Root{vhat[b].U, vhat[b].sig, vhat[b].rank, (int)(vt ? P.m[b] : P.n[b])});
+    if (P.stop_rows) {
+      build_band_recovery();
+      return;
+    }
 
     // ---------------------------------------------------- left-vector recovery
     // Y = X V_r = Q_y R_y, R_y = A S W^T  =>  U = Q_y A, V = V_r W.
@@ -1343,6 +1546,8 @@ hsvd_status build_plan(PlanImpl& P) {
   P.steps.clear();
   P.init_steps.clear();
   P.refine_steps.clear();
+  for (auto& v : P.stage_steps) v.clear();
+  P.roots.clear();
   P.blobs.clear();
   P.outs.clear();
   P.tmaps.clear();
@@ -1498,6 +1703,11 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   P.rank_tol = o.rank_tol > 0 ? o.rank_tol : (prec == HSVD_PREC_F64 ? 1e-12 : 1e-5);
   P.seed = o.seed ? o.seed : 0x1710028ull;
   P.host_staging = o.host_staging != 0;
+  if (o.stop_after_rows) {
+    // a band of a matrix split over ranks: one matrix, the paper's tree order
+    if (batch != 1 || tree != HSVD_TREE_COL_THEN_ROW) return HSVD_EINVAL;
+    P.stop_rows = true;
+  }
   P.elem = prec == HSVD_PREC_F64 ? 8 : 4;
   P.in_elem = in_dtype == HSVD_DTYPE_F64 ? 8 : (in_dtype == HSVD_DTYPE_F32 ? 4 : 2);
   P.tau = 50.0 * (prec == HSVD_PREC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
@@ -1771,6 +1981,8 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
 hsvd_status hsvd_run(hsvd_plan_t plan, const void* const* A, const int64_t* lda, void* stream) {
   if (!plan || !A || !lda) return HSVD_EINVAL;
   PlanImpl& P = plan->impl;
+  if (P.merge_only) return HSVD_EUNSUPPORTED;
+  P.stage_next = -1;
   for (int b = 0; b < P.batch; ++b)
     if (!A[b] || lda[b] < P.n[b]) return HSVD_EINVAL;
   return run_impl(plan, A, lda, static_cast<cudaStream_t>(stream));
@@ -1780,6 +1992,7 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
   if (!plan || !A || !lda) return HSVD_EINVAL;
   PlanImpl& P = plan->impl;
   if (!P.host_staging) return HSVD_EINVAL;
+  P.stage_next = -1;
   for (int b = 0; b < P.batch; ++b)
     if (!A[b] || lda[b] < P.n[b]) return HSVD_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1821,6 +2034,7 @@ hsvd_status hsvd_refine(hsvd_plan_t plan, int32_t max_iters, double eps, int32_t
                         void* stream) {
   if (!plan || max_iters < 1 || !(eps >= 0.0)) return HSVD_EINVAL;
   PlanImpl& P = plan->impl;
+  if (P.stop_rows || P.merge_only) return HSVD_EUNSUPPORTED;
   if (!P.ran) return HSVD_ENOTREADY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<double> err(P.batch, 0.0);
@@ -1867,9 +2081,12 @@ hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r) {
   r->max_rank = 0;
   if (P.ran) {
     int mn = 1 << 30, mx = 0;
-    for (auto& o : P.outs) {
+    // band plans before their recovery and merge plans: the row tree's ranks
+    const bool roots = P.merge_only || (P.stop_rows && P.stage_next < 3);
+    for (size_t i = 0; i < (roots ? P.roots.size() : P.outs.size()); ++i) {
+      const int* rp = roots ? P.roots[i].rank : P.outs[i].rank;
       int rk = 0;
-      if (cudaMemcpy(&rk, o.rank, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HSVD_ECUDA;
+      if (cudaMemcpy(&rk, rp, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HSVD_ECUDA;
       mn = std::min(mn, rk);
       mx = std::max(mx, rk);
     }
@@ -1888,7 +2105,8 @@ hsvd_status hsvd_factors(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* U, 
   const int64_t mo = P.m[idx], no = P.n[idx];
   if (U && ldu < mo) return HSVD_EINVAL;
   if (V && ldv < no) return HSVD_EINVAL;
-  if (!P.ran) return HSVD_ENOTREADY;
+  if (P.merge_only) return HSVD_EUNSUPPORTED;
+  if (!P.ran || (P.stop_rows && P.stage_next != 5)) return HSVD_ENOTREADY;
   const auto& po = P.outs[idx];
   // original orientation: U_orig (m rows), V_orig (n rows)
   void* su = po.trans ? po.V : po.U;
@@ -2027,6 +2245,223 @@ hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* ru
     for (int32_t i = 0; i < n && i < (int32_t)P.step_ms.size(); ++i) ms[i] = P.step_ms[i];
   if (runs) *runs = P.timed_runs;
   return HSVD_OK;
+}
+
+// ---------------------------------------------------------------- row split across ranks
+
+static hsvd_status run_list(PlanImpl& P, std::vector<hsvd::Step>& list, cudaStream_t s) {
+  P.last_error.clear();
+  for (auto& st : list) {
+    const cudaError_t e = st.run(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      P.last_error = st.name + ": " + cudaGetErrorString(e);
+      return HSVD_ECUDA;
+    }
+  }
+  P.last_stream = s;
+  return HSVD_OK;
+}
+
+static hsvd_status cuda_ok(PlanImpl& P, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HSVD_OK;
+  cudaGetLastError();
+  P.last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return HSVD_ECUDA;
+}
+
+hsvd_status hsvd_tree_root(hsvd_plan_t plan, int32_t idx, int32_t* rank, void* V, int64_t ldv, void* S,
+                           void* stream) {
+  if (!plan) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (idx < 0 || idx >= (int32_t)P.roots.size()) return HSVD_EINVAL;
+  const auto& rt = P.roots[idx];
+  if (V && ldv < rt.h) return HSVD_EINVAL;
+  if (!P.ran) return HSVD_ENOTREADY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int kc = P.kcap;
+  cudaError_t e = cudaSuccess;
+  if (V)
+    e = P.elem == 8 ? hsvd::launch_rowmajor_to_colmajor_full<double>(static_cast<double*>(rt.V), kc, rt.h, rt.rank,
+                                                                      kc, static_cast<double*>(V), ldv, s)
+                    : hsvd::launch_rowmajor_to_colmajor_full<float>(static_cast<float*>(rt.V), kc, rt.h, rt.rank, kc,
+                                                                     static_cast<float*>(V), ldv, s);
+  if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, rt.sig, P.elem * kc, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && rank) {
+    int rk = 0;
+    e = cudaMemcpyAsync(&rk, rt.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *rank = std::max(0, std::min(rk, kc));
+  }
+  return cuda_ok(P, e, "hsvd_tree_root");
+}
+
+hsvd_status hsvd_merge_plan(hsvd_plan_t* out, int64_t h, int32_t rank_cap, hsvd_trunc mode, double param,
+                            hsvd_prec prec, const hsvd_options* opts) {
+  if (!out) return HSVD_EINVAL;
+  *out = nullptr;
+  if (h < 1 || h > (int64_t(1) << 30) || rank_cap < 1 || rank_cap > 256 || !std::isfinite(param)) return HSVD_EINVAL;
+  switch (mode) {
+    case HSVD_TRUNC_FIXED_K:
+      if (param < 1 || param > 256 || param != std::floor(param)) return HSVD_EINVAL;
+      break;
+    case HSVD_TRUNC_GAMMA:
+      if (!(param > 0 && param < 1)) return HSVD_EINVAL;
+      break;
+    case HSVD_TRUNC_ENERGY:
+      if (!(param > 0 && param <= 1)) return HSVD_EINVAL;
+      break;
+    default: return HSVD_EINVAL;
+  }
+  if (prec != HSVD_PREC_F64 && prec != HSVD_PREC_F32 && prec != HSVD_PREC_BF16_MIXED) return HSVD_EINVAL;
+  hsvd_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.max_sweeps < 0 || std::isnan(o.rank_tol)) return HSVD_EINVAL;
+  std::unique_ptr<hsvd_plan_s> hp(new (std::nothrow) hsvd_plan_s());
+  if (!hp) return HSVD_ENOMEM;
+  PlanImpl& P = hp->impl;
+  P.batch = 1;
+  P.m.assign(1, h);
+  P.n.assign(1, h);
+  P.br = P.bc = h;
+  P.mode = mode;
+  P.param = param;
+  P.rank_cap = rank_cap;
+  P.prec = prec;
+  P.in_dtype = prec == HSVD_PREC_F64 ? HSVD_DTYPE_F64 : HSVD_DTYPE_F32;
+  const int base_k = mode == HSVD_TRUNC_FIXED_K ? (int)param : rank_cap;
+  P.kcap = std::min(rank_cap, base_k);
+  P.kp = P.kcap;
+  P.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
+  P.rank_tol = o.rank_tol > 0 ? o.rank_tol : (prec == HSVD_PREC_F64 ? 1e-12 : 1e-5);
+  P.elem = prec == HSVD_PREC_F64 ? 8 : 4;
+  P.in_elem = P.elem;
+  P.tau = 50.0 * (prec == HSVD_PREC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+  P.merge_only = true;
+  P.graph_off = true;
+  if (cudaGetDevice(&P.dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ECUDA;
+  }
+  if (cudaMalloc(&P.d_mats, sizeof(hsvd::MatRef)) != cudaSuccess ||
+      cudaMalloc(&P.d_status, sizeof(hsvd::DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  if (cudaMallocHost(&P.h_mats, sizeof(hsvd::MatRef)) != cudaSuccess) {
+    P.h_mats = nullptr;
+    cudaGetLastError();
+    return HSVD_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&P.mats_done, cudaEventDisableTiming) != cudaSuccess) return HSVD_ECUDA;
+  if (cudaMemset(P.d_status, 0, sizeof(hsvd::DevStatus)) != cudaSuccess) return HSVD_ECUDA;
+  const hsvd_status st =
+      prec == HSVD_PREC_F64 ? hsvd::build_plan<double, double>(P) : hsvd::build_plan<float, float>(P);
+  if (st != HSVD_OK) return st;
+  *out = hp.release();
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_merge_run(hsvd_plan_t plan, const void* V1, int64_t ld1, const void* S1, int32_t r1,
+                           const void* V2, int64_t ld2, const void* S2, int32_t r2, void* stream) {
+  if (!plan || !V1 || !S1 || !V2 || !S2) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (!P.merge_only) return HSVD_EINVAL;
+  const int h = (int)P.m[0], kc = P.kcap;
+  if (ld1 < h || ld2 < h || r1 < 0 || r2 < 0 || r1 > kc || r2 > kc) return HSVD_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const void* Vs[2] = {V1, V2};
+  const void* Ss[2] = {S1, S2};
+  const int64_t lds[2] = {ld1, ld2};
+  const int rs[2] = {r1, r2};
+  cudaError_t e = cudaMemsetAsync(P.d_status, 0, sizeof(hsvd::DevStatus), s);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = P.elem == 8 ? hsvd::launch_colmajor_to_rowmajor<double>(static_cast<const double*>(Vs[i]), lds[i], h, rs[i],
+                                                                kc, static_cast<double*>(P.min_.V[i]), s)
+                    : hsvd::launch_colmajor_to_rowmajor<float>(static_cast<const float*>(Vs[i]), lds[i], h, rs[i], kc,
+                                                               static_cast<float*>(P.min_.V[i]), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.min_.sig[i], 0, P.elem * kc, s);
+    if (e == cudaSuccess && rs[i] > 0) e = cudaMemcpyAsync(P.min_.sig[i], Ss[i], P.elem * rs[i], cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = hsvd::launch_set_words(P.min_.rank[i], rs[i], nullptr, 0, s);
+  }
+  const hsvd_status st = cuda_ok(P, e, "hsvd_merge_run inputs");
+  if (st != HSVD_OK) return st;
+  const hsvd_status rs2 = run_list(P, P.steps, s);
+  if (rs2 == HSVD_OK) P.ran = true;
+  return rs2;
+}
+
+// Stage entry points of a band plan (made with opts->stop_after_rows).
+static hsvd_status band_stage(hsvd_plan_t plan, int stage, const void* in, size_t in_bytes, void* in_dst,
+                              void* out, const void* out_src, size_t out_bytes, cudaStream_t s) {
+  PlanImpl& P = plan->impl;
+  if (!P.stop_rows) return HSVD_EINVAL;
+  if (!P.ran) return HSVD_ENOTREADY;
+  if (stage > 0 && P.stage_next != stage) return HSVD_ENOTREADY;
+  cudaError_t e = cudaSuccess;
+  if (in) e = cudaMemcpyAsync(in_dst, in, in_bytes, cudaMemcpyDeviceToDevice, s);
+  hsvd_status st = cuda_ok(P, e, "stage input");
+  if (st != HSVD_OK) return st;
+  st = run_list(P, P.stage_steps[stage], s);
+  if (st != HSVD_OK) return st;
+  if (out) st = cuda_ok(P, cudaMemcpyAsync(out, out_src, out_bytes, cudaMemcpyDeviceToDevice, s), "stage output");
+  if (st == HSVD_OK) P.stage_next = stage + 1;
+  return st;
+}
+
+hsvd_status hsvd_recover_begin(hsvd_plan_t plan, const void* Vhat, int64_t ldv, int32_t r, void* G, void* stream) {
+  if (!plan || !Vhat || !G) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (!P.stop_rows) return HSVD_EINVAL;
+  const int kc = P.kcap, nn = (int)P.n[0];
+  if (ldv < nn || r < 0 || r > kc) return HSVD_EINVAL;
+  if (!P.ran) return HSVD_ENOTREADY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e =
+      P.elem == 8 ? hsvd::launch_colmajor_to_rowmajor<double>(static_cast<const double*>(Vhat), ldv, nn, r, kc,
+                                                              static_cast<double*>(P.band.vin), s)
+                  : hsvd::launch_colmajor_to_rowmajor<float>(static_cast<const float*>(Vhat), ldv, nn, r, kc,
+                                                             static_cast<float*>(P.band.vin), s);
+  if (e == cudaSuccess) e = hsvd::launch_set_words(P.band.rin, r, nullptr, 0, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.band.G1, 0, P.elem * kc * kc, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.band.G2, 0, P.elem * kc * kc, s);
+  const hsvd_status st = cuda_ok(P, e, "hsvd_recover_begin inputs");
+  if (st != HSVD_OK) return st;
+  return band_stage(plan, 0, nullptr, 0, nullptr, G, P.band.G1, P.elem * kc * kc, s);
+}
+
+hsvd_status hsvd_recover_orth(hsvd_plan_t plan, const void* Gsum, void* G2, void* stream) {
+  if (!plan || !Gsum || !G2) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  const size_t b = P.elem * P.kcap * P.kcap;
+  return band_stage(plan, 1, Gsum, b, P.band.G1, G2, P.band.G2, b, static_cast<cudaStream_t>(stream));
+}
+
+hsvd_status hsvd_recover_core(hsvd_plan_t plan, const void* G2sum, void* absmax, void* stream) {
+  if (!plan || !G2sum || !absmax) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  const size_t b = P.elem * P.kcap * P.kcap;
+  return band_stage(plan, 2, G2sum, b, P.band.G2, absmax, P.band.amax, P.elem * P.kcap,
+                    static_cast<cudaStream_t>(stream));
+}
+
+hsvd_status hsvd_recover_signs(hsvd_plan_t plan, const void* absmax_all, int64_t row0, int64_t* key, void* stream) {
+  if (!plan || !absmax_all || !key || row0 < 0) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  if (!P.stop_rows) return HSVD_EINVAL;
+  if (P.stage_next != 3) return HSVD_ENOTREADY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const hsvd_status st = cuda_ok(P, hsvd::launch_set_words(nullptr, 0, P.band.row0, row0, s), "hsvd_recover_signs");
+  if (st != HSVD_OK) return st;
+  return band_stage(plan, 3, absmax_all, P.elem * P.kcap, P.band.amax, key, P.band.key, sizeof(int64_t) * P.kcap, s);
+}
+
+hsvd_status hsvd_recover_finish(hsvd_plan_t plan, const int64_t* key_min, void* stream) {
+  if (!plan || !key_min) return HSVD_EINVAL;
+  PlanImpl& P = plan->impl;
+  return band_stage(plan, 4, key_min, sizeof(int64_t) * P.kcap, P.band.key, nullptr, nullptr, 0,
+                    static_cast<cudaStream_t>(stream));
 }
 
 void hsvd_destroy(hsvd_plan_t plan) { delete plan; }

@@ -136,6 +136,98 @@ __global__ void k_rm_to_cm(const T* __restrict__ src, int64_t lds, int rows, con
   }
 }
 
+// ------------------------------------------------------------------ row split across ranks
+// Layout changes between the caller's column-major factors (rows x kcap,
+// zero columns past the rank) and the plan's row-major ones.
+template <class T>
+__global__ void k_cm_to_rm(const T* __restrict__ src, int64_t lds, int rows, int r, int kcap, T* __restrict__ dst) {
+  const int64_t total = (int64_t)rows * kcap;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / kcap, c = e % kcap;
+    dst[e] = c < r ? src[c * lds + i] : T(0);
+  }
+}
+template <class T>
+__global__ void k_rm_to_cm_full(const T* __restrict__ src, int64_t lds, int rows, const int* rank, int kcap,
+                                T* __restrict__ dst, int64_t ldd) {
+  const int r = min(*rank, kcap);
+  const int64_t total = (int64_t)rows * kcap;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, i = e % rows;
+    dst[c * ldd + i] = c < r ? src[i * lds + c] : T(0);
+  }
+}
+__global__ void k_set_words(int* p, int v, long long* q, long long w) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (p) *p = v;
+    if (q) *q = w;
+  }
+}
+// Per column c < rank of a band's U (rows x kcap row-major): the largest |U[i][c]|
+// (0 past the rank).  One CTA per column.
+template <class T>
+__global__ void __launch_bounds__(256) k_band_absmax(const T* __restrict__ U, int64_t ldu, int rows,
+                                                     const int* rank, int kcap, T* __restrict__ amax) {
+  __shared__ T red[256];
+  const int c = blockIdx.x;
+  const int r = min(*rank, kcap);
+  T best = T(0);
+  if (c < r)
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) best = max(best, (T)fabs(U[(int64_t)i * ldu + c]));
+  red[threadIdx.x] = best;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) amax[c] = red[0];
+}
+// key[c] = 2 (row0 + i) + (U[i][c] < 0) for the first row i of the band with
+// |U[i][c]| equal to amax_all[c] (the maximum over every band), else
+// INT64_MAX; the minimum over bands picks the first such row of the matrix.
+template <class T>
+__global__ void __launch_bounds__(256) k_band_keys(const T* __restrict__ U, int64_t ldu, int rows,
+                                                   const int* rank, int kcap, const T* __restrict__ amax_all,
+                                                   const long long* row0, long long* __restrict__ key) {
+  __shared__ int red[256];
+  const int c = blockIdx.x;
+  const int r = min(*rank, kcap);
+  const T target = amax_all[c];
+  int first = 0x7fffffff;
+  if (c < r && target > T(0))
+    for (int i = threadIdx.x; i < rows; i += blockDim.x)
+      if (fabs(U[(int64_t)i * ldu + c]) == target) {
+        first = i;
+        break;
+      }
+  red[threadIdx.x] = first;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int i = red[0];
+    key[c] = i == 0x7fffffff ? 0x7fffffffffffffffLL
+                             : 2LL * (*row0 + i) + (U[(int64_t)i * ldu + c] < T(0) ? 1 : 0);
+  }
+}
+// Negate U's and V's column c when the chosen entry (key[c]) is negative.
+template <class T>
+__global__ void __launch_bounds__(256) k_band_flip(T* __restrict__ U, int64_t ldu, int rows, T* __restrict__ V,
+                                                   int64_t ldv, int vrows, const int* rank, int kcap,
+                                                   const long long* __restrict__ key) {
+  const int c = blockIdx.x;
+  const int r = min(*rank, kcap);
+  if (c >= r) return;
+  const long long kk = key[c];
+  if (kk == 0x7fffffffffffffffLL || !(kk & 1)) return;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) U[(int64_t)i * ldu + c] = -U[(int64_t)i * ldu + c];
+  for (int i = threadIdx.x; i < vrows; i += blockDim.x) V[(int64_t)i * ldv + c] = -V[(int64_t)i * ldv + c];
+}
+
 inline int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 32) b = 152 * 32;
@@ -209,6 +301,51 @@ cudaError_t launch_rowmajor_to_colmajor(const T* src, int64_t lds, int rows, con
   k_rm_to_cm<T><<<grid_for((int64_t)rows * kcap, 256), 256, 0, s>>>(src, lds, rows, rank, kcap, dst, ldd);
   return cudaGetLastError();
 }
+
+template <class T>
+cudaError_t launch_colmajor_to_rowmajor(const T* src, int64_t lds, int rows, int r, int kcap, T* dst, cudaStream_t s) {
+  k_cm_to_rm<T><<<grid_for((int64_t)rows * kcap, 256), 256, 0, s>>>(src, lds, rows, r, kcap, dst);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_rowmajor_to_colmajor_full(const T* src, int64_t lds, int rows, const int* rank, int kcap, T* dst,
+                                             int64_t ldd, cudaStream_t s) {
+  k_rm_to_cm_full<T><<<grid_for((int64_t)rows * kcap, 256), 256, 0, s>>>(src, lds, rows, rank, kcap, dst, ldd);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_words(int* p, int v, long long* q, long long w, cudaStream_t s) {
+  k_set_words<<<1, 32, 0, s>>>(p, v, q, w);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_band_absmax(const T* U, int64_t ldu, int rows, const int* rank, int kcap, T* amax, cudaStream_t s) {
+  k_band_absmax<T><<<kcap, 256, 0, s>>>(U, ldu, rows, rank, kcap, amax);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_band_keys(const T* U, int64_t ldu, int rows, const int* rank, int kcap, const T* amax_all,
+                             const long long* row0, long long* key, cudaStream_t s) {
+  k_band_keys<T><<<kcap, 256, 0, s>>>(U, ldu, rows, rank, kcap, amax_all, row0, key);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_band_flip(T* U, int64_t ldu, int rows, T* V, int64_t ldv, int vrows, const int* rank, int kcap,
+                             const long long* key, cudaStream_t s) {
+  k_band_flip<T><<<kcap, 256, 0, s>>>(U, ldu, rows, V, ldv, vrows, rank, kcap, key);
+  return cudaGetLastError();
+}
+#define HSVD_BAND_INST(T)                                                                                         \
+  template cudaError_t launch_colmajor_to_rowmajor<T>(const T*, int64_t, int, int, int, T*, cudaStream_t);        \
+  template cudaError_t launch_rowmajor_to_colmajor_full<T>(const T*, int64_t, int, const int*, int, T*, int64_t, \
+                                                           cudaStream_t);                                         \
+  template cudaError_t launch_band_absmax<T>(const T*, int64_t, int, const int*, int, T*, cudaStream_t);          \
+  template cudaError_t launch_band_keys<T>(const T*, int64_t, int, const int*, int, const T*, const long long*,   \
+                                           long long*, cudaStream_t);                                             \
+  template cudaError_t launch_band_flip<T>(T*, int64_t, int, T*, int64_t, int, const int*, int, const long long*, \
+                                           cudaStream_t);
+HSVD_BAND_INST(float)
+HSVD_BAND_INST(double)
+#undef HSVD_BAND_INST
 
 template cudaError_t launch_block_energy<float, float>(const EnergyTask*, int, const MatRef*, cudaStream_t);
 template cudaError_t launch_block_energy<double, double>(const EnergyTask*, int, const MatRef*, cudaStream_t);

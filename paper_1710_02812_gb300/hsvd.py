@@ -27,7 +27,9 @@ EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd
             "hsvd_workspace_bytes", "hsvd_launches_per_run", "hsvd_destroy", "hsvd_error_string",
             "hsvd_tree_levels", "hsvd_jacobi_pair", "hsvd_step_count", "hsvd_step_info",
             "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error",
-            "hsvd_refine", "hsvd_gram")
+            "hsvd_refine", "hsvd_gram", "hsvd_tree_root", "hsvd_merge_plan", "hsvd_merge_run",
+            "hsvd_recover_begin", "hsvd_recover_orth", "hsvd_recover_core", "hsvd_recover_signs",
+            "hsvd_recover_finish")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -41,7 +43,8 @@ class HsvdError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32),
                 ("rank_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("max_sweeps", ctypes.c_int32), ("host_staging", ctypes.c_int32)]
+                ("max_sweeps", ctypes.c_int32), ("host_staging", ctypes.c_int32),
+                ("stop_after_rows", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -108,6 +111,18 @@ def lib():
         L.hsvd_refine.restype = ctypes.c_int
         L.hsvd_gram.argtypes = [P, i64, i64, i64, ctypes.c_int, P, i64, P]
         L.hsvd_gram.restype = ctypes.c_int
+        L.hsvd_tree_root.argtypes = [P, i32, ctypes.POINTER(i32), P, i64, P, P]
+        L.hsvd_merge_plan.argtypes = [ctypes.POINTER(P), i64, i32, ctypes.c_int, dbl, ctypes.c_int,
+                                      ctypes.POINTER(Options)]
+        L.hsvd_merge_run.argtypes = [P, P, i64, P, i32, P, i64, P, i32, P]
+        L.hsvd_recover_begin.argtypes = [P, P, i64, i32, P, P]
+        L.hsvd_recover_orth.argtypes = [P, P, P, P]
+        L.hsvd_recover_core.argtypes = [P, P, P, P]
+        L.hsvd_recover_signs.argtypes = [P, P, i64, P, P]
+        L.hsvd_recover_finish.argtypes = [P, P, P]
+        for f in ("hsvd_tree_root", "hsvd_merge_plan", "hsvd_merge_run", "hsvd_recover_begin",
+                  "hsvd_recover_orth", "hsvd_recover_core", "hsvd_recover_signs", "hsvd_recover_finish"):
+            getattr(L, f).restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
 
@@ -385,7 +400,7 @@ class Plan:
 
     def __init__(self, m, n, block_rows, block_cols, mode="fixed_k", param=10, rank_cap=None,
                  tree="col_then_row", prec="f32", in_dtype=None, oversample=0, power_iters=0,
-                 rank_tol=0.0, seed=0, max_sweeps=0, host_staging=False):
+                 rank_tol=0.0, seed=0, max_sweeps=0, host_staging=False, stop_after_rows=False):
         if isinstance(m, int):
             m, n = [m], [n]
         if rank_cap is None:
@@ -396,7 +411,7 @@ class Plan:
         self.rank_cap = int(rank_cap)
         self.kcap = min(self.rank_cap, int(param) if mode == "fixed_k" else self.rank_cap)
         opts = Options(int(oversample), int(power_iters), float(rank_tol), int(seed), int(max_sweeps),
-                       1 if host_staging else 0)
+                       1 if host_staging else 0, 1 if stop_after_rows else 0)
         self._h = hsvd_plan(self.m, self.n, block_rows, block_cols, mode, param, self.rank_cap, tree, prec,
                             self.in_dtype, opts)
 
@@ -465,6 +480,59 @@ class Plan:
         _check(code, "hsvd_factors")
         return r.value
 
+    # ---- one matrix split over ranks by row bands (a plan made with
+    # stop_after_rows=True factors one band up to its row tree)
+
+    def _ftype(self):
+        import torch
+        return torch.float64 if self.prec == "f64" else torch.float32
+
+    def tree_root(self, V, S, idx=0, stream=None) -> int:
+        """Row-tree result of matrix idx into device V (n x kcap column-major:
+        a kcap x n row-major tensor) and S (kcap); returns the rank."""
+        n = self.n[idx]
+        _check_dev(V, self._ftype(), self.kcap * n, "V")
+        _check_dev(S, self._ftype(), self.kcap, "S")
+        r = ctypes.c_int32()
+        _check(lib().hsvd_tree_root(self._h, idx, ctypes.byref(r), V.data_ptr(), n, S.data_ptr(),
+                                    _stream_ptr(stream)), "hsvd_tree_root")
+        return r.value
+
+    def recover_begin(self, Vhat, r, G, stream=None):
+        n, kc = self.n[0], self.kcap
+        _check_dev(Vhat, self._ftype(), kc * n, "Vhat")
+        _check_dev(G, self._ftype(), kc * kc, "G")
+        _check(lib().hsvd_recover_begin(self._h, Vhat.data_ptr(), n, int(r), G.data_ptr(), _stream_ptr(stream)),
+               "hsvd_recover_begin" + _detail(self._h))
+
+    def recover_orth(self, Gsum, G2, stream=None):
+        kc = self.kcap
+        _check_dev(Gsum, self._ftype(), kc * kc, "Gsum")
+        _check_dev(G2, self._ftype(), kc * kc, "G2")
+        _check(lib().hsvd_recover_orth(self._h, Gsum.data_ptr(), G2.data_ptr(), _stream_ptr(stream)),
+               "hsvd_recover_orth" + _detail(self._h))
+
+    def recover_core(self, G2sum, absmax, stream=None):
+        kc = self.kcap
+        _check_dev(G2sum, self._ftype(), kc * kc, "G2sum")
+        _check_dev(absmax, self._ftype(), kc, "absmax")
+        _check(lib().hsvd_recover_core(self._h, G2sum.data_ptr(), absmax.data_ptr(), _stream_ptr(stream)),
+               "hsvd_recover_core" + _detail(self._h))
+
+    def recover_signs(self, absmax_all, row0, key, stream=None):
+        import torch
+        kc = self.kcap
+        _check_dev(absmax_all, self._ftype(), kc, "absmax_all")
+        _check_dev(key, torch.int64, kc, "key")
+        _check(lib().hsvd_recover_signs(self._h, absmax_all.data_ptr(), int(row0), key.data_ptr(),
+                                        _stream_ptr(stream)), "hsvd_recover_signs" + _detail(self._h))
+
+    def recover_finish(self, key_min, stream=None):
+        import torch
+        _check_dev(key_min, torch.int64, self.kcap, "key_min")
+        _check(lib().hsvd_recover_finish(self._h, key_min.data_ptr(), _stream_ptr(stream)),
+               "hsvd_recover_finish" + _detail(self._h))
+
     def refine(self, max_iters=3, eps=1e-3, stream=None):
         """Alg. 2 on the last run's factors, in place; returns (passes, Error)."""
         return hsvd_refine(self._h, max_iters, eps, stream)
@@ -488,3 +556,64 @@ class Plan:
 
     def step_times(self):
         return hsvd_step_times(self._h)
+
+
+def _check_dev(t, dtype, need, name):
+    """A contiguous CUDA tensor of the given type holding at least `need`
+    elements (the C side reads or writes that many)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: a CUDA tensor is required")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, {dtype} required")
+    if not t.is_contiguous() or t.numel() < need:
+        raise ValueError(f"{name}: a contiguous tensor of at least {need} elements is required")
+
+
+class MergePlan:
+    """hsvd_merge_plan: one MAT merge of two factor pairs of height h."""
+
+    def __init__(self, h, mode="fixed_k", param=10, rank_cap=None, prec="f32", rank_tol=0.0, max_sweeps=0):
+        if rank_cap is None:
+            rank_cap = int(param) if mode == "fixed_k" else 128
+        self.h, self.prec = int(h), prec
+        self.kcap = min(int(rank_cap), int(param) if mode == "fixed_k" else int(rank_cap))
+        opts = Options(0, 0, float(rank_tol), 0, int(max_sweeps), 0, 0)
+        hnd = ctypes.c_void_p()
+        _check(lib().hsvd_merge_plan(ctypes.byref(hnd), self.h, int(rank_cap), TRUNC[mode], float(param),
+                                     PREC[prec], ctypes.byref(opts)), "hsvd_merge_plan")
+        self._h = hnd
+
+    def _ftype(self):
+        import torch
+        return torch.float64 if self.prec == "f64" else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            hsvd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, V1, S1, r1, V2, S2, r2, stream=None):
+        """V1, V2: device h x kcap column-major (kcap x h row-major tensors)."""
+        for name, t, need in (("V1", V1, self.kcap * self.h), ("V2", V2, self.kcap * self.h),
+                              ("S1", S1, max(1, int(r1))), ("S2", S2, max(1, int(r2)))):
+            _check_dev(t, self._ftype(), need, name)
+        _check(lib().hsvd_merge_run(self._h, V1.data_ptr(), self.h, S1.data_ptr(), int(r1), V2.data_ptr(), self.h,
+                                    S2.data_ptr(), int(r2), _stream_ptr(stream)), "hsvd_merge_run" + _detail(self._h))
+
+    def root(self, V, S, stream=None) -> int:
+        _check_dev(V, self._ftype(), self.kcap * self.h, "V")
+        _check_dev(S, self._ftype(), self.kcap, "S")
+        r = ctypes.c_int32()
+        _check(lib().hsvd_tree_root(self._h, 0, ctypes.byref(r), V.data_ptr(), self.h, S.data_ptr(),
+                                    _stream_ptr(stream)), "hsvd_tree_root")
+        return r.value
+
+    def status(self, sync=True):
+        return hsvd_status_query(self._h, sync)
