@@ -497,7 +497,7 @@ def run_ours(args, world, rank, local):
     ms = reduce_max(world, ms, dev)
     jac_ms, jac_runs = plan.step_times()
     plan.set_timing(1)
-    for _ in range(2):
+    for _ in range(0 if args.quick else 2):
         plan.run([xd], stream=stream)
     step_ms, runs = plan.step_times()
     plan.set_timing(False)
@@ -516,23 +516,26 @@ def run_ours(args, world, rank, local):
 
     # ---- end to end through the C ABI with host buffers: pinned input read by
     # hsvd_run_host, factors copied back to the host every step
-    xh = torch.empty((M, N), dtype=torch.float32, pin_memory=True)
-    xh.copy_(xd)
-    for _ in range(max(1, args.warmup // 2)):
-        plan.run_host([xh], stream=stream)
-        plan.factors(0, stream=stream)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        plan.run_host([xh], stream=stream)
-        plan.factors(0, stream=stream)
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-    e2e_ms = reduce_max(world, e2e_ms, dev)
+    e2e_ms = float("nan")
+    if not args.quick:
+        xh = torch.empty((M, N), dtype=torch.float32, pin_memory=True)
+        xh.copy_(xd)
+        for _ in range(max(1, args.warmup // 2)):
+            plan.run_host([xh], stream=stream)
+            plan.factors(0, stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.run_host([xh], stream=stream)
+            plan.factors(0, stream=stream)
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+        e2e_ms = reduce_max(world, e2e_ms, dev)
+        del xh
     h2d = M * N * 4
     d2h = (M + N) * plan.kcap * 4 + plan.kcap * 4 + 4
     launches = plan.launches_per_run
     plan.close()
-    del plan, xh
+    del plan
     torch.cuda.empty_cache()
 
     # ---- roofline of the dominant kernel family (device time per run)
@@ -543,7 +546,11 @@ def run_ours(args, world, rank, local):
         f["flops"] += info["flops"]
         f["bytes"] += info["bytes"]
         f["launches"] += 1
-    dom = max(fam, key=lambda k: fam[k]["ms"])
+    if runs == 0:  # --quick: no per-step pass; the live core-SVD times only
+        for f in fam.values():
+            f["ms"] = 0.0
+        fam.setdefault("jacobi", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+    dom = "jacobi" if runs == 0 else max(fam, key=lambda k: fam[k]["ms"])
     pk, pk_src = peaks()
     d = fam[dom]
     jac_live = sum(t for info, t in zip(steps, jac_ms) if info["kind"] == "jacobi") / max(1, jac_runs)
@@ -638,6 +645,76 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_split_rows(args, world, rank, local):
+    """--split rows: ONE matrix of the workload over the ranks, each holding a
+    band of whole row slabs (rowsplit.factor_rows: band plans, the merge tree
+    over ranks by point-to-point factor sends, V_hat broadcast, CholeskyQR2
+    of the recovery with the Grams summed over the bands).  value = m n 4 /
+    max rank time ("strong" scaling: the total work is fixed)."""
+    import torch
+    from paper_1710_02812_gb300 import rowsplit
+    from paper_1710_02812_gb300 import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    q = args.power_iters
+    row0, rows = rowsplit.band_rows(M, BR, world)[rank]
+    xb = W.planted_device(M, N, spectrum()[:min(MODES, M, N)], noise=NOISE, tag=TAG, device=dev,
+                          rows=(row0, row0 + rows))
+    band = rowsplit.DeviceBand(xb, N, row0, BR, BC, K, prec=args.prec, power_iters=q)
+    comm = rowsplit.TorchComm() if world > 1 else rowsplit.SingleComm()
+    for _ in range(args.warmup):
+        rowsplit.factor_rows(band, comm)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        u, s, v = rowsplit.factor_rows(band, comm)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    ms = reduce_max(world, e0.elapsed_time(e1) / args.steps, dev)
+    # end to end: this rank's band from page-locked host memory, the factors
+    # (its U rows, S, V) back to the host every step
+    xh = torch.empty((rows, N), dtype=torch.float32, pin_memory=True)
+    xh.copy_(xb)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xb.copy_(xh, non_blocking=True)
+        u, s, v = rowsplit.factor_rows(band, comm)
+        u, s, v = u.cpu(), s.cpu(), v.cpu()
+    e2e_ms = reduce_max(world, 1e3 * (time.perf_counter() - t0) / args.steps, dev)
+    st = band.plan.status()
+    value = M * N * 4 / (ms * 1e-3) / 1e9
+    line = {"metric": "input GB/s (rank-k SVD, top-k sigma rel err <= 1e-4)", "value": value, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "time_to_rank_k_ms": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": {"f32": "f32", "bf16_mixed": "bf16"}[args.prec], "data": "synthetic",
+            "config": dict(workload_config(args.prec, q), split="rows", bands=rowsplit.band_rows(M, BR, world)),
+            "e2e": {"value": M * N * 4 / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": rows * N * 4, "d2h_bytes_per_step": (rows + N + 1) * band.kc * 4,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": None, "clocks": clocks, "status": st, "roofline": None, "cpu_baseline": None,
+            "note": "one matrix split by row bands; the roofline and CPU baseline are on the default single-"
+                    "matrix line"}
+    band.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -649,10 +726,18 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparison run")
     ap.add_argument("--power-iters", dest="power_iters", type=int, default=1)
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy measures and the CPU baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="the timed steps only (no accuracy, CPU baseline, comparison, end-to-end or per-step "
+                         "pass): for profiler launch lists")
+    ap.add_argument("--split", default="none", choices=["none", "rows"],
+                    help="rows: one matrix over the ranks by row bands (strong scaling); "
+                         "none: every rank its own matrix (weak scaling)")
     ap.add_argument("--size", type=int, default=65536,
                     help="matrix size (default 65536, the bench workload; smaller sizes are for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.quick:
+        args.no_oracle = args.no_compare = True
     if args.size != 65536:
         if args.size < BR or args.size % BR:
             ap.error(f"--size must be a multiple of the {BR}-row block")
@@ -661,6 +746,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
+        if args.split == "rows":
+            return run_split_rows(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

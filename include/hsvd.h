@@ -100,6 +100,11 @@ typedef struct {
   int32_t stop_after_rows; /* nonzero: a band plan (one matrix, COL_THEN_ROW): hsvd_run
                               stops after the row MAT tree, whose result hsvd_tree_root
                               returns; U is recovered with the hsvd_recover_* stages */
+  int32_t autotune;     /* nonzero: the first run times the candidate kernels of every
+                           core-SVD launch and the pipeline depths of every tensor-core
+                           product on this plan's own data and keeps the fastest (see
+                           hsvd_step_variant); later runs and plans of the same shape
+                           reuse the choices */
 } hsvd_options;
 
 /* Device status words, read back by hsvd_status_query. */
@@ -238,6 +243,13 @@ int32_t hsvd_step_count(hsvd_plan_t plan);
  * output pointer may be NULL.  EINVAL for a bad index. */
 hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* kind,
                            int32_t* tasks, int32_t* dim, double* flops, double* bytes);
+
+/* hsvd_step_variant -- the kernel variant step i runs (NUL-terminated name,
+ * truncated to name_len; "default" for a step without variants) and the
+ * number of candidates the autotuner compares for it (0 or 1: none).
+ * Before the first run of an autotuned plan the name is the default's.
+ * EINVAL for a bad index. */
+hsvd_status hsvd_step_variant(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* count);
 
 /* hsvd_set_timing -- per-step device times of the following runs (CUDA
  * events on the run's stream): on = 1 around every step, on = 2 around the

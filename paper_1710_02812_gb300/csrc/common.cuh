@@ -6,6 +6,8 @@
 // launch covers a whole level of Alg. 1 for every matrix of the batch.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -171,9 +173,15 @@ cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem
 template <class T>
 cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
                         cudaStream_t s, bool with_product);
+// Kernels of a core launch (autotuning); JV_AUTO is the default dispatch.
+enum { JV_AUTO = 0, JV_BP1 = 1, JV_BP2 = 2, JV_SPLIT = 3, JV_CLUSTER = 4, JV_SM4 = 5, JV_SM8 = 6, JV_SM16 = 7 };
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
-                          TruncParams tp, DevStatus* st, cudaStream_t s);
+                          TruncParams tp, DevStatus* st, cudaStream_t s, int variant = JV_AUTO);
+std::vector<int> jacobi_variants(int nrcap, int nccap, bool want_v, size_t elem);
+const char* jacobi_variant_name(int v);
+bool jacobi_bp_fits(int nrcap, int nccap, bool want_v);
+bool jacobi_bp_two_per_sm(int nrcap, int nccap, bool want_v);
 
 cudaError_t launch_fill_gaussian_f32(float* out, int64_t count, uint64_t seed, cudaStream_t s);
 cudaError_t launch_fill_gaussian_f64(double* out, int64_t count, uint64_t seed, cudaStream_t s);
@@ -261,7 +269,8 @@ cudaError_t launch_make_bt(const BtTask* tasks, const int3* items, int nitems, c
 cudaError_t launch_convert_input(const void* X, bool x_is_bf16, int64_t ld, int64_t m, int64_t n, __nv_bfloat16* Xb,
                                  int64_t ldx, __nv_bfloat16* Xt, int64_t ldxt, cudaStream_t s);
 cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int bmax, int* err,
-                           cudaStream_t s);
+                           cudaStream_t s, int stages_override = 0);
+std::vector<int> tc_stage_variants(int bmax);
 
 // Host-side helpers exported for checks without a GPU.
 int jacobi_pair_host(int n, int r, int s, int* p, int* q);
@@ -293,7 +302,7 @@ cudaError_t launch_band_flip(T* U, int64_t ldu, int rows, T* V, int64_t ldv, int
 cudaError_t launch_jacobi_split(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                                 TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
-                             TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
+                             TruncParams tp, DevStatus* st, cudaStream_t s, bool* done, int force_minb);
 size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem);
 bool chol_uses_smem(int kcap, size_t elem);
 

@@ -295,7 +295,7 @@ static size_t jacobi_bp_bytes(int rmax, int nccap, bool want_v) {
          sizeof(float);
 }
 cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
-                             TruncParams tp, DevStatus* st, cudaStream_t s, bool* done) {
+                             TruncParams tp, DevStatus* st, cudaStream_t s, bool* done, int force_minb) {
   *done = false;
   if (!jacobi_bp_enabled() || nccap < 8 || nccap > 128 || nrcap > 128) return cudaSuccess;
   const int rows = nrcap <= 32 ? 32 : nrcap <= 64 ? 64 : 128;
@@ -328,8 +328,9 @@ cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrc
     }
     return v > 0 ? v : 152;
   }();
-  if (f2 && !want_v && rmax == 16 && ntasks > nsm && 2 * (bytes + 8 * 1024) <= 220 * 1024)
-    return go(k_jacobi_bp<false, 16, true, 2>);
+  const bool two_fit = f2 && !want_v && rmax == 16 && 2 * (bytes + 8 * 1024) <= 220 * 1024;
+  if (force_minb == 2 && !two_fit) return cudaSuccess;
+  if (two_fit && (force_minb == 2 || (force_minb == 0 && ntasks > nsm))) return go(k_jacobi_bp<false, 16, true, 2>);
   if (f2) {
     switch (rmax * 2 + (want_v ? 1 : 0)) {
       case 8: return go(k_jacobi_bp<false, 4, true>);
@@ -352,4 +353,17 @@ cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrc
   }
 }
 
+}  // namespace hsvd
+
+namespace hsvd {
+// Whether the two-CTAs-per-SM form of the block-pair kernel applies.
+bool jacobi_bp_two_per_sm(int nrcap, int nccap, bool want_v) {
+  if (!jacobi_bp_enabled() || want_v || nccap < 8 || nccap > 128 || nrcap <= 64 || nrcap > 128) return false;
+  return 2 * (jacobi_bp_bytes(16, nccap, false) + 8 * 1024) <= 220 * 1024;
+}
+bool jacobi_bp_fits(int nrcap, int nccap, bool want_v) {
+  if (!jacobi_bp_enabled() || nccap < 8 || nccap > 128 || nrcap > 128) return false;
+  const int rows = nrcap <= 32 ? 32 : nrcap <= 64 ? 64 : 128;
+  return jacobi_bp_bytes(rows / 8, nccap, want_v) <= 200 * 1024;
+}
 }  // namespace hsvd

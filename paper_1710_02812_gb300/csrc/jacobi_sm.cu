@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include <cstdlib>
+#include <vector>
 
 #include "common.cuh"
 #include "jacobi.cuh"
@@ -499,7 +500,7 @@ static cudaError_t launch_jacobi_v(const JacobiTask<T>* tasks, int ntasks, int n
 }
 
 // Shared-memory variant: lanes per pair and rows per lane from the row cap.
-static bool jacobi_sm_shape(int nrcap, int& G, int& rmax) {
+static bool jacobi_sm_shape(int nrcap, int& G, int& rmax, int force_g = 0) {
   // Lanes per pair: fewer lanes mean less replicated rotation arithmetic and
   // shorter shuffle reductions, more lanes more warps to hide latency.
   // HSVD_JACOBI_LANES (4, 8 or 16) overrides the default of 8 for tuning.
@@ -510,7 +511,8 @@ static bool jacobi_sm_shape(int nrcap, int& G, int& rmax) {
   }();
   if (nrcap > 256) return false;
   const int rows = nrcap <= 32 ? 32 : nrcap <= 64 ? 64 : nrcap <= 128 ? 128 : 256;
-  G = lanes;
+  G = force_g > 0 ? force_g : lanes;
+  if (force_g > 0 && (rows / force_g > 32 || rows / force_g < 4)) return false;
   while (rows / G > 32) G *= 2;  // at most 32 rows per lane
   rmax = rows / G;
   if (rmax < 4) {
@@ -532,10 +534,10 @@ bool jacobi_sm_fits(int nrcap, int nccap, bool want_v, size_t elem) {
 
 template <class T, bool V>
 static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, TruncParams tp,
-                                   DevStatus* st, cudaStream_t s, bool* done) {
+                                   DevStatus* st, cudaStream_t s, bool* done, int force_g = 0) {
   *done = false;
   int G, rmax;
-  if (!jacobi_sm_shape(nrcap, G, rmax)) return cudaSuccess;
+  if (!jacobi_sm_shape(nrcap, G, rmax, force_g)) return cudaSuccess;
   const int ncc = nccap + (nccap & 1);
   const size_t bytes = ((size_t)jacobi_ld_g(G * rmax, (int)sizeof(T), G) * ncc +
                         (V ? (size_t)jacobi_ld(ncc, (int)sizeof(T)) * ncc : 0)) *
@@ -571,13 +573,31 @@ static cudaError_t launch_jacobi_sm(const JacobiTask<T>* tasks, int ntasks, int 
 
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
-                          TruncParams tp, DevStatus* st, cudaStream_t s) {
+                          TruncParams tp, DevStatus* st, cudaStream_t s, int variant) {
   if (ntasks <= 0) return cudaSuccess;
   if (nccap > 512 || nrcap > 512) return cudaErrorInvalidValue;
   bool done = false;
   cudaError_t e = cudaSuccess;
+  if (variant != JV_AUTO) {
+    // a forced kernel (autotuning): it must apply to this launch
+    if constexpr (sizeof(T) == 4) {
+      if (variant == JV_BP1 || variant == JV_BP2)
+        e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, variant == JV_BP1 ? 1 : 2);
+      else if (variant == JV_SPLIT)
+        e = launch_jacobi_split(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
+      else if (variant == JV_CLUSTER)
+        e = launch_jacobi_cluster(tasks, ntasks, nrcap, nccap, want_v, 2, tp, st, s, &done);
+    }
+    if (variant == JV_SM4 || variant == JV_SM8 || variant == JV_SM16) {
+      const int g = variant == JV_SM4 ? 4 : (variant == JV_SM8 ? 8 : 16);
+      e = want_v ? launch_jacobi_sm<T, true>(tasks, ntasks, nrcap, nccap, tp, st, s, &done, g)
+                 : launch_jacobi_sm<T, false>(tasks, ntasks, nrcap, nccap, tp, st, s, &done, g);
+    }
+    if (e != cudaSuccess) return e;
+    return done ? cudaSuccess : cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 4) {
-    e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
+    e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, 0);
     if (e != cudaSuccess || done) return e;
     // Cores one CTA cannot hold are spread over a cluster: by columns (two
     // CTAs, columns exchanged twice per sweep), else by rows.
@@ -609,9 +629,49 @@ bool jacobi_uses_smem(int nrcap, int nccap, bool want_v, size_t elem) {
   return jacobi_work_bytes(nrcap, nccap, want_v, elem) <= 200 * 1024;
 }
 
+// Kernels that can run a core launch (autotuning candidates); the first is
+// the default dispatch.
+std::vector<int> jacobi_variants(int nrcap, int nccap, bool want_v, size_t elem) {
+  std::vector<int> v{JV_AUTO};
+  if (nccap > 512 || nrcap > 512) return v;
+  if (elem == 4) {
+    if (jacobi_bp_fits(nrcap, nccap, want_v)) {
+      v.push_back(JV_BP1);
+      if (jacobi_bp_two_per_sm(nrcap, nccap, want_v)) v.push_back(JV_BP2);
+    }
+    if (!want_v && nccap > 128 && nccap <= 256 && nrcap <= 256) v.push_back(JV_SPLIT);
+    if (nccap > 128 && nccap <= 256 && nrcap <= 256 && jacobi_cluster_smem(nrcap, nccap, want_v, 2) > 0 &&
+        jacobi_cluster_smem(nrcap, nccap, want_v, 2) <= 200 * 1024)
+      v.push_back(JV_CLUSTER);
+  }
+  for (int g : {4, 8, 16}) {
+    int G, rmax;
+    if (!jacobi_sm_shape(nrcap, G, rmax, g)) continue;
+    const int ncc = nccap + (nccap & 1);
+    const size_t bytes = ((size_t)jacobi_ld_g(G * rmax, (int)elem, G) * ncc +
+                          (want_v ? (size_t)jacobi_ld(ncc, (int)elem) * ncc : 0)) * elem;
+    if (bytes <= 200 * 1024) v.push_back(g == 4 ? JV_SM4 : (g == 8 ? JV_SM8 : JV_SM16));
+  }
+  return v;
+}
+
+const char* jacobi_variant_name(int v) {
+  switch (v) {
+    case JV_AUTO: return "jacobi:default";
+    case JV_BP1: return "jacobi:block-pair, 1 CTA/SM";
+    case JV_BP2: return "jacobi:block-pair, 2 CTAs/SM";
+    case JV_SPLIT: return "jacobi:column-split cluster";
+    case JV_CLUSTER: return "jacobi:row-split cluster";
+    case JV_SM4: return "jacobi:shared memory, 4 lanes/pair";
+    case JV_SM8: return "jacobi:shared memory, 8 lanes/pair";
+    case JV_SM16: return "jacobi:shared memory, 16 lanes/pair";
+  }
+  return "jacobi:?";
+}
+
 template cudaError_t launch_jacobi<float>(const JacobiTask<float>*, int, int, int, bool, TruncParams, DevStatus*,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template cudaError_t launch_jacobi<double>(const JacobiTask<double>*, int, int, int, bool, TruncParams,
-                                           DevStatus*, cudaStream_t);
+                                           DevStatus*, cudaStream_t, int);
 
 }  // namespace hsvd

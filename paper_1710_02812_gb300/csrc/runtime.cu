@@ -16,6 +16,8 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
+#include <map>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -51,6 +53,11 @@ struct Blob {
 struct Step {
   std::string name;
   std::function<cudaError_t(cudaStream_t)> run;
+  // Tunable steps: run() launches variant *choice of variant_names (the
+  // kernels or pipeline depths that can do the launch); the autotuner times
+  // them on the first run and keeps the fastest.
+  std::shared_ptr<int> choice;
+  std::vector<std::string> variant_names;
   bool varies = false;  // its launch arguments change from run to run (kept out of the graph)
   int kind = 0;   // hsvd_step_kind
   int tasks = 0;  // tasks (blocks / merges / slabs / matrices) in the launch
@@ -142,6 +149,8 @@ struct PlanImpl {
   // row MAT tree (stop_rows) and recovers U in stages whose sums over the
   // bands the caller makes between them; a merge plan holds one MAT merge of
   // two factors (merge_only).
+  bool autotune = false;  // time the variants of tunable steps on the first run
+  bool tuned = false;
   bool stop_rows = false;
   bool merge_only = false;
   struct Root {
@@ -659,10 +668,19 @@ struct Builder {
                              return launch_make_bt(p->table<BtTask>(b1), p->table<int3>(b2), n2, s);
                            }});
     tag(9, (int)ops.size(), bmax, 0, (double)ops.size() * bmax * kpad * 2 * per);
-    P.steps.push_back(Step{name, [p, b3, b4, n4, bmax](cudaStream_t s) {
-                             return launch_tc_gemm(p->d_tmaps, p->table<TcTask>(b3), p->table<TcItem>(b4), n4, bmax,
-                                                   &p->d_status->tc_timeouts, s);
-                           }});
+    {
+      const std::vector<int> depths = tc_stage_variants(bmax);
+      auto choice = std::make_shared<int>(0);
+      P.steps.push_back(Step{name, [p, b3, b4, n4, bmax, depths, choice](cudaStream_t s) {
+                               const int st = depths.empty() ? 0 : depths[(size_t)*choice % depths.size()];
+                               return launch_tc_gemm(p->d_tmaps, p->table<TcTask>(b3), p->table<TcItem>(b4), n4,
+                                                     bmax, &p->d_status->tc_timeouts, s, st);
+                             }});
+      if (depths.size() > 1) {
+        P.steps.back().choice = choice;
+        for (int d : depths) P.steps.back().variant_names.push_back("tc_gemm:" + std::to_string(d) + " stages");
+      }
+    }
     tag(8, (int)ops.size(), bmax, flops, bytes);
     if (!red.empty()) {
       const size_t b5 = P.add_blob(red), b6 = P.add_blob(rdi);
@@ -709,10 +727,20 @@ struct Builder {
     PlanImpl* p = &P;
     const size_t bt = P.add_blob(tasks);
     const int nt = (int)tasks.size();
-    P.steps.push_back(Step{name, [p, bt, nt, nrcap, nccap, want_v, tp](cudaStream_t s) {
+    // the global-memory kernels need the work buffers above; the others are
+    // candidates only when the default keeps the core on chip
+    std::vector<int> vars{JV_AUTO};
+    if (jacobi_uses_smem(nrcap, nccap, want_v, sizeof(T)) || (sizeof(T) == 4 && nccap > 128 && nccap <= 256))
+      vars = jacobi_variants(nrcap, nccap, want_v, sizeof(T));
+    auto choice = std::make_shared<int>(0);
+    P.steps.push_back(Step{name, [p, bt, nt, nrcap, nccap, want_v, tp, vars, choice](cudaStream_t s) {
                              return launch_jacobi<T>(p->table<JacobiTask<T>>(bt), nt, nrcap, nccap, want_v, tp,
-                                                     p->d_status, s);
+                                                     p->d_status, s, vars[(size_t)*choice % vars.size()]);
                            }});
+    if (vars.size() > 1) {
+      P.steps.back().choice = choice;
+      for (int v : vars) P.steps.back().variant_names.push_back(jacobi_variant_name(v));
+    }
     {
       // Algorithmic flops of an SVD of an n x n core: 22 n^3, the count the
       // paper uses for the merge core (Section 3.1: 176 k^3 for 2k x 2k).
@@ -1585,7 +1613,9 @@ hsvd_status build_plan(PlanImpl& P) {
   if (cudaMemcpy(P.tables, host.data(), P.tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return HSVD_ECUDA;
   for (auto& st : P.init_steps)
     if (st.run(nullptr) != cudaSuccess) return HSVD_ECUDA;
-  if (cudaDeviceSynchronize() != cudaSuccess) return HSVD_ECUDA;
+  // the init steps ran on the legacy default stream (a device-wide
+  // synchronise would fail while another thread captures a CUDA graph)
+  if (cudaStreamSynchronize(nullptr) != cudaSuccess) return HSVD_ECUDA;
   P.launches_per_run = (int)P.steps.size();
   return HSVD_OK;
 }
@@ -1703,6 +1733,7 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   P.rank_tol = o.rank_tol > 0 ? o.rank_tol : (prec == HSVD_PREC_F64 ? 1e-12 : 1e-5);
   P.seed = o.seed ? o.seed : 0x1710028ull;
   P.host_staging = o.host_staging != 0;
+  P.autotune = o.autotune != 0;
   if (o.stop_after_rows) {
     // a band of a matrix split over ranks: one matrix, the paper's tree order
     if (batch != 1 || tree != HSVD_TREE_COL_THEN_ROW) return HSVD_EINVAL;
@@ -1757,6 +1788,83 @@ hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const i
   return HSVD_OK;
 }
 
+// Process-wide choices of the autotuner, by step name, launch size and
+// candidates (plans of the same shape reuse them).
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static std::string tune_key(const PlanImpl& P, const hsvd::Step& st) {
+  std::string k = st.name + "|" + std::to_string(st.tasks) + "|" + std::to_string(st.dim) + "|" +
+                  std::to_string(P.elem);
+  for (const auto& n : st.variant_names) k += "|" + n;
+  return k;
+}
+
+// The autotuner: run the steps in order; at a tunable step, launch each
+// variant once (warm-up), then three times between two events, keep the
+// fastest (ties: the earlier, the default first), and leave its outputs for
+// the next step.  Core and product launches do not modify their inputs, so
+// repeating them is safe.  The choices are kept for the plan's later runs
+// (and its CUDA graph) and for other plans with the same steps.
+static hsvd_status autotune_pass(PlanImpl& P, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return HSVD_ECUDA;
+  }
+  hsvd_status out = HSVD_OK;
+  for (auto& st : P.steps) {
+    if (st.choice && st.variant_names.size() > 1) {
+      const std::string key = tune_key(P, st);
+      int pick = -1;
+      {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) pick = it->second;
+      }
+      if (pick < 0) {
+        float best = 0.f;
+        for (size_t v = 0; v < st.variant_names.size(); ++v) {
+          *st.choice = (int)v;
+          if (st.run(s) != cudaSuccess) {  // not applicable to this launch
+            cudaGetLastError();
+            continue;
+          }
+          cudaEventRecord(e0, s);
+          bool ok = true;
+          for (int r = 0; r < 3 && ok; ++r) ok = st.run(s) == cudaSuccess;
+          cudaEventRecord(e1, s);
+          if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (pick < 0 || ms < best) {
+            best = ms;
+            pick = (int)v;
+          }
+        }
+        if (pick < 0) pick = 0;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = pick;
+      }
+      *st.choice = pick;
+    }
+    const cudaError_t e = st.run(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      P.last_error = st.name + ": " + cudaGetErrorString(e);
+      out = HSVD_ECUDA;
+      break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out == HSVD_OK) P.tuned = true;
+  return out;
+}
+
 static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_t* lda, cudaStream_t s) {
   PlanImpl& P = plan->impl;
   if (cudaEventSynchronize(P.mats_done) != cudaSuccess) return HSVD_ECUDA;
@@ -1776,6 +1884,13 @@ static hsvd_status run_impl(hsvd_plan_t plan, const void* const* A, const int64_
     return HSVD_ECUDA;
   if (cudaEventRecord(P.mats_done, s) != cudaSuccess) return HSVD_ECUDA;
   if (cudaMemsetAsync(P.d_status, 0, sizeof(hsvd::DevStatus), s) != cudaSuccess) return HSVD_ECUDA;
+  if (P.autotune && !P.tuned) {
+    // the first run tunes (its repeated launches count in the status words,
+    // which are cleared again before the run proper)
+    const hsvd_status ts = autotune_pass(P, s);
+    if (ts != HSVD_OK) return ts;
+    if (cudaMemsetAsync(P.d_status, 0, sizeof(hsvd::DevStatus), s) != cudaSuccess) return HSVD_ECUDA;
+  }
   const bool trace = std::getenv("HSVD_TRACE") != nullptr;
   const bool timed = P.timing || trace;
   std::vector<cudaEvent_t> ev;
@@ -2223,6 +2338,21 @@ hsvd_status hsvd_step_info(hsvd_plan_t plan, int32_t i, char* name, int32_t name
   if (dim) *dim = st.dim;
   if (flops) *flops = st.flops;
   if (bytes) *bytes = st.bytes;
+  return HSVD_OK;
+}
+
+hsvd_status hsvd_step_variant(hsvd_plan_t plan, int32_t i, char* name, int32_t name_len, int32_t* count) {
+  if (!plan) return HSVD_EINVAL;
+  const PlanImpl& P = plan->impl;
+  if (i < 0 || i >= (int32_t)P.steps.size()) return HSVD_EINVAL;
+  const auto& st = P.steps[i];
+  const int n = (int)st.variant_names.size();
+  if (count) *count = n;
+  if (name && name_len > 0) {
+    const std::string v = (st.choice && n > 0) ? st.variant_names[(size_t)*st.choice % n] : std::string("default");
+    std::strncpy(name, v.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
   return HSVD_OK;
 }
 

@@ -17,6 +17,8 @@
 // its own copies and MMAs (again bounded), frees its TMEM and returns.
 #include <cuda.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace hsvd {
@@ -363,11 +365,19 @@ int tc_stages(int bmax) {
   return st;
 }
 
+// Pipeline depths that fit for a B width (autotuning candidates; the
+// default, the deepest, first).
+std::vector<int> tc_stage_variants(int bmax) {
+  std::vector<int> v;
+  for (int st = tc_stages(bmax); st >= 2; --st) v.push_back(st);
+  return v;
+}
+
 cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int bmax,
-                           int* err, cudaStream_t s) {
+                           int* err, cudaStream_t s, int stages_override) {
   if (nitems <= 0) return cudaSuccess;
   if (bmax < 16 || bmax > 256 || (bmax & 15)) return cudaErrorInvalidValue;
-  const int stages = tc_stages(bmax);
+  const int stages = stages_override >= 2 && stages_override <= tc_stages(bmax) ? stages_override : tc_stages(bmax);
   const size_t bytes = tc_smem_bytes(stages, bmax);
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;

@@ -29,7 +29,7 @@ EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd
             "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error",
             "hsvd_refine", "hsvd_gram", "hsvd_tree_root", "hsvd_merge_plan", "hsvd_merge_run",
             "hsvd_recover_begin", "hsvd_recover_orth", "hsvd_recover_core", "hsvd_recover_signs",
-            "hsvd_recover_finish")
+            "hsvd_recover_finish", "hsvd_step_variant")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32),
                 ("rank_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("max_sweeps", ctypes.c_int32), ("host_staging", ctypes.c_int32),
-                ("stop_after_rows", ctypes.c_int32)]
+                ("stop_after_rows", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -120,6 +120,8 @@ def lib():
         L.hsvd_recover_core.argtypes = [P, P, P, P]
         L.hsvd_recover_signs.argtypes = [P, P, i64, P, P]
         L.hsvd_recover_finish.argtypes = [P, P, P]
+        L.hsvd_step_variant.argtypes = [P, i32, ctypes.c_char_p, i32, ctypes.POINTER(i32)]
+        L.hsvd_step_variant.restype = ctypes.c_int
         for f in ("hsvd_tree_root", "hsvd_merge_plan", "hsvd_merge_run", "hsvd_recover_begin",
                   "hsvd_recover_orth", "hsvd_recover_core", "hsvd_recover_signs", "hsvd_recover_finish"):
             getattr(L, f).restype = ctypes.c_int
@@ -400,7 +402,8 @@ class Plan:
 
     def __init__(self, m, n, block_rows, block_cols, mode="fixed_k", param=10, rank_cap=None,
                  tree="col_then_row", prec="f32", in_dtype=None, oversample=0, power_iters=0,
-                 rank_tol=0.0, seed=0, max_sweeps=0, host_staging=False, stop_after_rows=False):
+                 rank_tol=0.0, seed=0, max_sweeps=0, host_staging=False, stop_after_rows=False,
+                 autotune=False):
         if isinstance(m, int):
             m, n = [m], [n]
         if rank_cap is None:
@@ -411,7 +414,7 @@ class Plan:
         self.rank_cap = int(rank_cap)
         self.kcap = min(self.rank_cap, int(param) if mode == "fixed_k" else self.rank_cap)
         opts = Options(int(oversample), int(power_iters), float(rank_tol), int(seed), int(max_sweeps),
-                       1 if host_staging else 0, 1 if stop_after_rows else 0)
+                       1 if host_staging else 0, 1 if stop_after_rows else 0, 1 if autotune else 0)
         self._h = hsvd_plan(self.m, self.n, block_rows, block_cols, mode, param, self.rank_cap, tree, prec,
                             self.in_dtype, opts)
 
@@ -551,6 +554,16 @@ class Plan:
     def steps(self):
         return [hsvd_step_info(self._h, i) for i in range(hsvd_step_count(self._h))]
 
+    def variants(self):
+        """Per step: (name, chosen variant, number of candidates)."""
+        out = []
+        for i in range(hsvd_step_count(self._h)):
+            buf = ctypes.create_string_buffer(96)
+            cnt = ctypes.c_int32()
+            _check(lib().hsvd_step_variant(self._h, i, buf, 96, ctypes.byref(cnt)), "hsvd_step_variant")
+            out.append((hsvd_step_info(self._h, i)["name"], buf.value.decode(), cnt.value))
+        return out
+
     def set_timing(self, on=True):
         hsvd_set_timing(self._h, on)
 
@@ -578,7 +591,7 @@ class MergePlan:
             rank_cap = int(param) if mode == "fixed_k" else 128
         self.h, self.prec = int(h), prec
         self.kcap = min(int(rank_cap), int(param) if mode == "fixed_k" else int(rank_cap))
-        opts = Options(0, 0, float(rank_tol), 0, int(max_sweeps), 0, 0)
+        opts = Options(0, 0, float(rank_tol), 0, int(max_sweeps), 0, 0, 0)
         hnd = ctypes.c_void_p()
         _check(lib().hsvd_merge_plan(ctypes.byref(hnd), self.h, int(rank_cap), TRUNC[mode], float(param),
                                      PREC[prec], ctypes.byref(opts)), "hsvd_merge_plan")

@@ -96,6 +96,23 @@ def factor_rows(band, comm):
     return band.factors()
 
 
+class SingleComm:
+    """comm of a single rank: nothing to exchange."""
+
+    rank, world = 0, 1
+
+    def send(self, t, dst):
+        raise RuntimeError("a single rank sends nothing")
+
+    recv = send
+
+    def broadcast(self, t, src):
+        pass
+
+    def all_reduce(self, t, op):
+        pass
+
+
 class TorchComm:
     """comm for factor_rows over torch.distributed (NCCL for CUDA tensors,
     gloo for host tensors)."""

@@ -189,10 +189,12 @@ def orthonormal_device(m: int, r: int, g, device):
 
 
 def planted_device(m: int, n: int, s, noise: float = 0.0, tag: int = 0, device="cuda",
-                   chunk_rows: int = 4096):
+                   chunk_rows: int = 4096, rows=None):
     """A = U diag(s) V^T + noise * N(0, 1) as FP32 on the device (U, V with
     orthonormal columns; the noise-free part has singular values exactly s
-    up to FP32 storage)."""
+    up to FP32 storage).  rows = (r0, r1): only those rows of the same
+    matrix (the noise of the other chunks is still drawn, to keep the
+    generator's stream)."""
     import torch
     s = torch.as_tensor(np.asarray(s, dtype=np.float64), device=device)
     g = _torch_gen(tag, device)
@@ -200,13 +202,18 @@ def planted_device(m: int, n: int, s, noise: float = 0.0, tag: int = 0, device="
     v = orthonormal_device(n, s.numel(), g, device)
     us = (u * s[None, :]).to(torch.float32)
     vt = v.t().contiguous().to(torch.float32)
-    a = torch.empty((m, n), dtype=torch.float32, device=device)
+    b0, b1 = (0, m) if rows is None else (int(rows[0]), int(rows[1]))
+    a = torch.empty((b1 - b0, n), dtype=torch.float32, device=device)
     for r0 in range(0, m, chunk_rows):
         r1 = min(m, r0 + chunk_rows)
-        blk = us[r0:r1] @ vt
-        if noise:
-            blk += noise * torch.randn((r1 - r0, n), generator=g, device=device, dtype=torch.float32)
-        a[r0:r1] = blk
+        lo, hi = max(r0, b0), min(r1, b1)
+        nz = noise * torch.randn((r1 - r0, n), generator=g, device=device, dtype=torch.float32) if noise else None
+        if lo >= hi:
+            continue
+        blk = us[lo:hi] @ vt
+        if nz is not None:
+            blk += nz[lo - r0:hi - r0]
+        a[lo - b0:hi - b0] = blk
     return a
 
 

@@ -592,3 +592,27 @@ def test_planner_limits(m, n, br, bc, k, prec):
     ref = oracle_run(xin, br, bc, "fixed_k", k, prec)
     gate = s_true if prec != "bf16_mixed" else s_true[s_true >= 0.05]
     check(xin, got, ref, prec, f"limits {m}x{n}/{br}x{bc} k={k} {prec}", s_true=gate)
+
+
+def test_autotune_picks_measured_variants_and_keeps_parity():
+    """hsvd_options.autotune: the first run times the candidate kernels of
+    each core-SVD launch and the pipeline depths of each tensor-core product,
+    keeps the fastest, and the result still matches the oracle; later runs
+    replay the same choices (bitwise-identical factors)."""
+    x = W.exp_decay(1024, 1024, r=300, noise=1e-5, tag=71, dtype=np.float32)
+    plan = hsvd.Plan(1024, 1024, 256, 256, "fixed_k", 64, prec="bf16_mixed", power_iters=1, autotune=True)
+    xd = torch.from_numpy(x).cuda()
+    plan.run([xd])
+    u1, s1, v1 = plan.factors(0)
+    tuned = [v for v in plan.variants() if v[2] > 1]
+    assert any(v[1].startswith("jacobi:") for v in tuned), tuned
+    assert any(v[1].startswith("tc_gemm:") for v in tuned), tuned
+    plan.run([xd])
+    u2, s2, v2 = plan.factors(0)
+    np.testing.assert_array_equal(s1, s2)
+    np.testing.assert_array_equal(u1, u2)
+    xb = W.bf16_round(x)
+    ref = oracle_run(xb, 256, 256, "fixed_k", 64, "bf16_mixed")
+    check(xb, (u1, s1, v1), ref, "bf16_mixed", "autotuned", s_true=np.exp(-np.arange(300) / 20.0))
+    st = plan.status()
+    assert st["not_converged"] == 0 and st["nonfinite"] == 0 and st["tensor_timeouts"] == 0

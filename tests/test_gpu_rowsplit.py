@@ -80,11 +80,20 @@ def run_split(x, world, br, bc, k, prec, **kw):
               "q": {(a, b): queue.Queue() for a in range(world) for b in range(world)}}
     results, errors = [None] * world, []
     bands = rowsplit.band_rows(m, br, world)
+    first_run = threading.Lock()
 
     def rank_main(r):
         try:
             row0, rows = bands[r]
-            band = rowsplit.DeviceBand(xd[row0:row0 + rows], n, row0, br, bc, k, prec=prec, **kw)
+            # a plan's first run captures its CUDA graph: plans are made and
+            # first run one thread at a time, and every thread waits for all of
+            # them before the split (a device-wide synchronise of one thread
+            # may not overlap another's capture)
+            with first_run:
+                band = rowsplit.DeviceBand(xd[row0:row0 + rows], n, row0, br, bc, k, prec=prec, **kw)
+                band.plan.run([band.x])
+                torch.cuda.synchronize()
+            shared["bar"].wait(timeout=300)
             u, s, v = rowsplit.factor_rows(band, ThreadComm(shared, r))
             results[r] = (u.cpu().numpy(), s.cpu().numpy(), v.cpu().numpy(), band.plan.status())
             band.close()
