@@ -484,7 +484,8 @@ def run_ours(args, world, rank, local):
     # core-SVD (Jacobi) launches inside the replayed graph (the dominant
     # family's live time); the per-family split comes from an instrumented
     # pass after the timed region
-    plan = hsvd.Plan(M, N, BR, BC, "fixed_k", K, prec=args.prec, power_iters=q, host_staging=True)
+    plan = hsvd.Plan(M, N, BR, BC, "fixed_k", K, prec=args.prec, power_iters=q, host_staging=True,
+                     autotune=not args.no_autotune)
     for _ in range(args.warmup):
         plan.run([xd], stream=stream)
     torch.cuda.synchronize(dev)
@@ -534,6 +535,10 @@ def run_ours(args, world, rank, local):
     h2d = M * N * 4
     d2h = (M + N) * plan.kcap * 4 + plan.kcap * 4 + 4
     launches = plan.launches_per_run
+    tuned = {}
+    for name, chosen, cnt in plan.variants():
+        if cnt > 1:
+            tuned[chosen] = tuned.get(chosen, 0) + 1
     plan.close()
     del plan
     torch.cuda.empty_cache()
@@ -587,7 +592,7 @@ def run_ours(args, world, rank, local):
     # ---- the other side of "mixed vs plain FP32": same workload, FP32 path
     compare = None
     if not args.no_compare and args.prec != "f32":
-        pf = hsvd.Plan(M, N, BR, BC, "fixed_k", K, prec="f32", power_iters=q)
+        pf = hsvd.Plan(M, N, BR, BC, "fixed_k", K, prec="f32", power_iters=q, autotune=not args.no_autotune)
         for _ in range(args.warmup):
             pf.run([xd], stream=stream)
         torch.cuda.synchronize(dev)
@@ -626,7 +631,8 @@ def run_ours(args, world, rank, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "time_to_rank_k_ms": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"f32": "f32", "bf16_mixed": "bf16"}[args.prec], "data": "synthetic",
-            "config": workload_config(args.prec, q),
+            "config": dict(workload_config(args.prec, q),
+                           autotuned={"on": not args.no_autotune, "launches_by_choice": tuned}),
             "roofline": roof,
             "kernel_families_ms": {k: round(v["ms"], 4) for k, v in sorted(fam.items(), key=lambda kv: -kv[1]["ms"])},
             "kernel_families_note": "instrumented pass after the timed region: events around every step",
@@ -726,6 +732,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparison run")
     ap.add_argument("--power-iters", dest="power_iters", type=int, default=1)
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy measures and the CPU baseline")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
+                    help="default kernels instead of the autotuner's choices (timed on the first warm-up run)")
     ap.add_argument("--quick", action="store_true",
                     help="the timed steps only (no accuracy, CPU baseline, comparison, end-to-end or per-step "
                          "pass): for profiler launch lists")

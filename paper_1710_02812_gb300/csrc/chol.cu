@@ -507,11 +507,16 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
         if (t % CB_NW != warp) continue;
         float* T = tiles + t * CB_TS;
         const int c = 32 * J + lane;
+        float v[32];  // all 32 loads of the tile in flight before the stores
+#pragma unroll
         for (int r = 0; r < 32; ++r) {
           const int i = 32 * I + r;
-          float v = 0.f;
-          if (i < k && c < k && c >= i) v = tk.G[(int64_t)i * tk.ldg + c] * sc[i] * sc[c];
-          T[r * CB_LD + lane] = v;
+          v[r] = (i < k && c < k && c >= i) ? tk.G[(int64_t)i * tk.ldg + c] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int i = 32 * I + r;
+          T[r * CB_LD + lane] = (i < k && c < k) ? v[r] * sc[i] * sc[c] : 0.f;
         }
       }
   }

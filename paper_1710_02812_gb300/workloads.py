@@ -179,13 +179,15 @@ def _torch_gen(tag: int, device):
 
 
 def orthonormal_device(m: int, r: int, g, device):
-    """Q factor (diag(R) > 0) of a seeded m x r Gaussian, FP64 on the device."""
+    """Q factor (diag(R) > 0) of a seeded m x r Gaussian, FP64 on the device
+    (the Gaussian drawn on the device, the QR by LAPACK on the host, so the
+    recipe needs no device linear-algebra library)."""
     import torch
-    a = torch.randn((m, r), generator=g, device=device, dtype=torch.float64)
-    q, rr = torch.linalg.qr(a)
-    d = torch.sign(torch.diagonal(rr))
+    a = torch.randn((m, r), generator=g, device=device, dtype=torch.float64).cpu().numpy()
+    q, rr = np.linalg.qr(a)
+    d = np.sign(np.diag(rr))
     d[d == 0] = 1
-    return q * d[None, :]
+    return torch.from_numpy(q * d[None, :]).to(device)
 
 
 def planted_device(m: int, n: int, s, noise: float = 0.0, tag: int = 0, device="cuda",
