@@ -56,10 +56,11 @@ NOISE = 1e-6
 TAG = 5
 ORACLE_SIZE = 8192          # the recipe at this size is compared with the oracle
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
-# DRAM bytes per launch of the dominant kernels, from ncu captures of the
-# current kernels (dram__bytes_read.sum + dram__bytes_write.sum), per unit of
-# work; None where no capture of the current kernel exists
-TRAFFIC_PER_UNIT = {}
+# DRAM bytes per unit of work of the dominant kernels, from ncu captures of
+# the current kernels (dram__bytes_read.sum + dram__bytes_write.sum): the
+# core SVDs per core (two launches of k_jacobi_cs at 8192^2: 23.31 MB over
+# 96 cores of 256 x 256); absent where no capture of the current kernel exists
+TRAFFIC_PER_UNIT = {"jacobi": (16867840 + 23552 + 6416128) / 96}
 
 
 def spectrum():
@@ -582,7 +583,11 @@ def run_ours(args, world, rank, local):
         roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": "derived FP32 peak",
                 "work": "k^3 flops per k x k factorisation and inverse"}
-    roof["traffic"] = traffic * d["launches"] if traffic else None
+    # per launch, like achieved: the family's units (cores) per launch x bytes per unit
+    roof["traffic"] = (traffic * st["jacobi_cores"] / max(1, d["launches"])
+                       if traffic and dom == "jacobi" else None)
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = "ncu DRAM bytes per core (k_jacobi_cs, 8192^2 capture) x cores per launch"
     roof["share_of_step"] = d["ms"] / ms
     roof["launches_per_step"] = d["launches"]
     roof["ms_per_step"] = d["ms"]

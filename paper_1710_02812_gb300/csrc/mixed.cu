@@ -46,39 +46,52 @@ __global__ void __launch_bounds__(256) k_convert_input(const TI* __restrict__ X,
   }
 }
 
-// FP32 input with rows 16-byte aligned: 32 x 128 tiles read as float4 (four
-// times fewer, larger requests, which matters when X is read in place from
-// host memory over NVLink-C2C), written as BF16 to X and, transposed, to X^T.
+// FP32 input with rows 16-byte aligned: 64 x 128 tiles, every thread's
+// eight float4 loads issued before any store (many requests in flight, which
+// matters most when X is read in place from host memory over NVLink-C2C),
+// X written as packed 8-byte groups of BF16, X^T through a shared tile of
+// row pairs (two BF16 of consecutive rows in one 32-bit word) so each lane
+// writes two consecutive elements of an X^T row.
 __global__ void __launch_bounds__(256) k_convert_input4(const float* __restrict__ X, int64_t ld, int64_t m,
                                                         int64_t n, __nv_bfloat16* __restrict__ Xb, int64_t ldx,
                                                         __nv_bfloat16* __restrict__ Xt, int64_t ldxt) {
-  __shared__ __nv_bfloat16 tile[32][128 + 2];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 128;
+  __shared__ uint32_t pairs[32][128 + 1];  // row pair p, column c: rows 2p (low half) and 2p + 1
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 64, c0 = static_cast<int64_t>(blockIdx.x) * 128;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i, c = c0 + 4 * tx;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < m && c < n) v = *reinterpret_cast<const float4*>(X + r * ld + c);  // n % 4 == 0
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
-    const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
-    if (r < m && c < n) {
-      __nv_bfloat16* d = Xb + r * ldx + c;
-      d[0] = b0;
-      d[1] = b1;
-      d[2] = b2;
-      d[3] = b3;
-    }
-    tile[i][4 * tx] = b0;
-    tile[i][4 * tx + 1] = b1;
-    tile[i][4 * tx + 2] = b2;
-    tile[i][4 * tx + 3] = b3;
+  const int64_t c = c0 + 4 * tx;
+  float4 v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t r = r0 + ty + 8 * j;
+    v[j] = (r < m && c < n) ? *reinterpret_cast<const float4*>(X + r * ld + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int i = ty + 8 * j;
+    const int64_t r = r0 + i;
+    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(v[j].x, v[j].y);
+    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(v[j].z, v[j].w);
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&lo2), w1 = *reinterpret_cast<const uint32_t*>(&hi2);
+    if (r < m && c < n) *reinterpret_cast<uint2*>(Xb + r * ldx + c) = make_uint2(w0, w1);  // n, ldx % 4 == 0
+    unsigned short* t = reinterpret_cast<unsigned short*>(&pairs[i >> 1][0]) + (i & 1);
+    t[2 * (4 * tx + 0)] = static_cast<unsigned short>(w0 & 0xffffu);
+    t[2 * (4 * tx + 1)] = static_cast<unsigned short>(w0 >> 16);
+    t[2 * (4 * tx + 2)] = static_cast<unsigned short>(w1 & 0xffffu);
+    t[2 * (4 * tx + 3)] = static_cast<unsigned short>(w1 >> 16);
   }
   __syncthreads();
   if (!Xt) return;
-  for (int e = threadIdx.x; e < 128 * 32; e += 256) {
-    const int cc = e >> 5, rr = e & 31;  // X^T row c0 + cc, column r0 + rr
-    const int64_t c = c0 + cc, r = r0 + rr;
-    if (c < n && r < m) Xt[c * ldxt + r] = tile[rr][cc];
+  const int64_t r = r0 + 2 * tx;  // this lane's two X^T columns (rows of X)
+  for (int cc = ty; cc < 128; cc += 8) {
+    const int64_t col = c0 + cc;  // X^T row
+    if (col >= n || r >= m) continue;
+    const uint32_t w = pairs[tx][cc];
+    __nv_bfloat16* d = Xt + col * ldxt + r;
+    if (r + 1 < m) {
+      *reinterpret_cast<uint32_t*>(d) = w;  // ldxt even, r even: 4-byte aligned
+    } else {
+      *reinterpret_cast<unsigned short*>(d) = static_cast<unsigned short>(w & 0xffffu);
+    }
   }
 }
 
@@ -118,7 +131,7 @@ cudaError_t launch_convert_input(const void* X, bool x_is_bf16, int64_t ld, int6
     k_convert_input<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(X), ld, m, n, Xb, ldx, Xt,
                                                         ldxt);
   } else if (n % 4 == 0 && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
-    dim3 g4(static_cast<unsigned>((n + 127) / 128), static_cast<unsigned>((m + 31) / 32));
+    dim3 g4(static_cast<unsigned>((n + 127) / 128), static_cast<unsigned>((m + 63) / 64));
     k_convert_input4<<<g4, 256, 0, s>>>(static_cast<const float*>(X), ld, m, n, Xb, ldx, Xt, ldxt);
   } else {
     k_convert_input<float><<<grid, 256, 0, s>>>(static_cast<const float*>(X), ld, m, n, Xb, ldx, Xt, ldxt);
