@@ -116,7 +116,7 @@ typedef struct {
   int32_t max_rank;       /* largest final rank over the batch */
   int32_t jacobi_sweeps;  /* one-sided Jacobi sweeps summed over all cores */
   int32_t jacobi_cores;   /* number of Jacobi cores solved */
-  int32_t tensor_timeouts; /* tensor-core GEMM tiles whose bounded waits ran out (results invalid) */
+  int32_t tensor_timeouts; /* tensor-core GEMM CTAs whose bounded waits ran out (results invalid) */
 } hsvd_report;
 
 typedef struct hsvd_plan_s* hsvd_plan_t;

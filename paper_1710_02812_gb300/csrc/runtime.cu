@@ -2192,6 +2192,7 @@ hsvd_status hsvd_status_query(hsvd_plan_t plan, int32_t sync, hsvd_report* r) {
   r->nonfinite = ds.nonfinite;
   r->jacobi_sweeps = ds.sweeps;
   r->jacobi_cores = ds.cores;
+  r->tensor_timeouts = ds.tc_timeouts;
   r->min_rank = 0;
   r->max_rank = 0;
   if (P.ran) {

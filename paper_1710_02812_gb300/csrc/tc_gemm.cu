@@ -6,16 +6,21 @@
 // part of a factor split hi + lo, accumulated into the same tensor-memory
 // accumulator, which gives the projections near-FP32 accuracy.
 //
-// One CTA computes one 128-row tile of one task for all N (<= 256) columns:
+// A CTA computes 128-row tiles (items) of the tasks for all N (<= 256)
+// columns, persistently:
 //   warp 0, one thread : TMA loads of the A / B tiles (128B swizzle) into a
 //                        ring of stages, completion on "full" mbarriers;
 //   warp 1, one thread : tcgen05.mma (kind::f16, M = 128, N = Nmma, K = 16
-//                        per instruction) into TMEM; tcgen05.commit frees a
-//                        stage ("empty") and finally signals "done";
-//   warps 0-3          : tcgen05.ld of their 32 TMEM lanes, FP32 stores.
+//                        per instruction) into one of two TMEM accumulators;
+//                        tcgen05.commit frees a stage ("empty") and marks an
+//                        accumulator full;
+//   warps 2-5          : tcgen05.ld of their 32 TMEM lanes, FP32 stores,
+//                        then the accumulator is marked empty again.
 // Every wait is bounded: on timeout the CTA raises an error flag, waits for
 // its own copies and MMAs (again bounded), frees its TMEM and returns.
 #include <cuda.h>
+
+#include <cstdlib>
 
 #include <vector>
 
@@ -144,29 +149,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restrict__ maps,
+// Persistent form: a CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+// with a stage ring that runs on across items and two TMEM accumulators, so
+// the epilogue of one item (warps 2-5 read their TMEM lane quarter and store)
+// runs under the loads and MMAs of the next (warps 0 and 1).  Barriers:
+// full/empty per stage (TMA -> MMA -> TMA), tfull/tempty per accumulator
+// (MMA -> epilogue -> MMA).  Every wait is bounded; after a timeout every role
+// stops, the producer waits (bounded) for its copies in flight, the issuer
+// for its MMAs, and the CTA frees its TMEM.  first_wait (test only, 0 = off)
+// shortens the issuer's first wait so the timeout path can be exercised.
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const CUtensorMap* __restrict__ maps,
                                                     const TcTask* __restrict__ tasks,
-                                                    const TcItem* __restrict__ items, int stages, int bmax,
-                                                    int* __restrict__ err) {
+                                                    const TcItem* __restrict__ items, int nitems, int stages,
+                                                    int bmax, int* __restrict__ err, long long first_wait) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8];
   __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
 
-  const TcItem it = items[blockIdx.x];
-  const TcTask tk = tasks[it.task];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool has_lo = tk.b2_row0 >= 0;
-  const int nk_all = (tk.K + TC_BK - 1) / TC_BK;
-  const int kt0 = tk.kchunk_tiles > 0 ? it.kc * tk.kchunk_tiles : 0;
-  const int nk = tk.kchunk_tiles > 0 ? min(nk_all - kt0, tk.kchunk_tiles) : nk_all;  // >= 1 by construction
   const uint32_t a_bytes = TC_BM * TC_BK * 2;
   const uint32_t b_bytes = static_cast<uint32_t>(bmax) * TC_BK * 2;
   const uint32_t stage_bytes = a_bytes + 2u * b_bytes;
-  const uint32_t ncols = bmax <= 32 ? 32 : bmax <= 64 ? 64 : bmax <= 128 ? 128 : 256;
-  // 1024-byte aligned ring of stages: [A | B | B2]
+  const uint32_t acc_cols = bmax <= 32 ? 32 : bmax <= 64 ? 64 : bmax <= 128 ? 128 : 256;
+  const uint32_t ncols = 2 * acc_cols;  // two accumulators
   const uint32_t base_s = (smem_u32(smem_raw) + 1023u) & ~1023u;
   unsigned char* base = smem_raw + (base_s - smem_u32(smem_raw));
 
@@ -174,6 +184,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp
     }
     mbar_init(&done_bar, 1);
     failed = 0;
@@ -184,94 +198,153 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const CUtensorMap* __restric
   __syncthreads();
   tc_fence_after();
   const uint32_t tacc = tmem_base;
-  const CUtensorMap* amap = maps + tk.amap;
-  const CUtensorMap* bmap = maps + tk.bmap;
-  const int arow = tk.a_row0 + it.mt * TC_BM;
+  auto fail = [&]() {  // counts the CTAs whose waits ran out
+    if (atomicExch(&failed, 1) == 0) atomicAdd(err, 1);
+  };
+  auto chunk = [&](const TcTask& tk, const TcItem& it, int& kt0, int& nk) {
+    const int nk_all = (tk.K + TC_BK - 1) / TC_BK;
+    kt0 = tk.kchunk_tiles > 0 ? it.kc * tk.kchunk_tiles : 0;
+    nk = tk.kchunk_tiles > 0 ? min(nk_all - kt0, tk.kchunk_tiles) : nk_all;  // >= 1 by construction
+  };
 
-  int issued = 0;   // producer: tiles issued
-  int mma_done = 0; // issuer: stages committed
-  if (warp == 0 && lane == 0) {
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % stages;
-      if (kt >= stages && !mbar_wait(&empty_bar[s], ((kt / stages) - 1) & 1)) {
-        atomicExch(&failed, 1);
-        break;
+  if (warp == 0) {
+    // ---- producer: TMA loads of every item's K tiles into the stage ring
+    int g = 0;  // stages issued by this CTA
+    if (lane == 0) {
+      for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x) {
+        const TcItem it = items[i];
+        const TcTask tk = tasks[it.task];
+        int kt0, nk;
+        chunk(tk, it, kt0, nk);
+        const bool has_lo = tk.b2_row0 >= 0;
+        const CUtensorMap* amap = maps + tk.amap;
+        const CUtensorMap* bmap = maps + tk.bmap;
+        const int arow = tk.a_row0 + it.mt * TC_BM;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % stages;
+          if (g >= stages && !mbar_wait(&empty_bar[s], ((g / stages) - 1) & 1)) {
+            fail();
+            break;
+          }
+          if (*(volatile int*)&failed) break;
+          unsigned char* st = base + s * stage_bytes;
+          mbar_arrive_expect_tx(&full_bar[s], a_bytes + (has_lo ? 2u : 1u) * b_bytes);
+          const int kx = (kt0 + kt) * TC_BK;
+          tma_load_2d(st, amap, &full_bar[s], tk.a_col0 + kx, arow);
+          tma_load_2d(st + a_bytes, bmap, &full_bar[s], kx, tk.b_row0);
+          if (has_lo) tma_load_2d(st + a_bytes + b_bytes, bmap, &full_bar[s], kx, tk.b2_row0);
+        }
       }
-      if (*(volatile int*)&failed) break;
-      unsigned char* st = base + s * stage_bytes;
-      mbar_arrive_expect_tx(&full_bar[s], a_bytes + (has_lo ? 2u : 1u) * b_bytes);
-      const int kx = (kt0 + kt) * TC_BK;
-      tma_load_2d(st, amap, &full_bar[s], tk.a_col0 + kx, arow);
-      tma_load_2d(st + a_bytes, bmap, &full_bar[s], kx, tk.b_row0);
-      if (has_lo) tma_load_2d(st + a_bytes + b_bytes, bmap, &full_bar[s], kx, tk.b2_row0);
-      ++issued;
+      if (*(volatile int*)&failed) {
+        // copies still in flight land before the shared memory is released
+        for (int t = g > stages ? g - stages : 0; t < g; ++t) mbar_wait(&full_bar[t % stages], (t / stages) & 1);
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16_f32(TC_BM, bmax);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % stages;
-      if (!mbar_wait(&full_bar[s], (kt / stages) & 1)) {
-        atomicExch(&failed, 1);
+  } else if (warp == 1) {
+    // ---- MMA issuer: each item into accumulator (j & 1)
+    if (lane == 0) {
+      int g = 0, j = 0;
+      bool first = true;
+      for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x, ++j) {
+        const TcItem it = items[i];
+        const TcTask tk = tasks[it.task];
+        int kt0, nk;
+        chunk(tk, it, kt0, nk);
+        const bool has_lo = tk.b2_row0 >= 0;
+        const int a = j & 1;
+        if (j >= 2 && !mbar_wait(&tempty_bar[a], ((j >> 1) - 1) & 1)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tacc + static_cast<uint32_t>(a) * acc_cols;
+        const uint32_t idesc = idesc_bf16_f32(TC_BM, bmax);
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % stages;
+          bool got;
+          if (first && first_wait > 0) {
+            const long long t0 = clock64();
+            got = mbar_test(&full_bar[s], (g / stages) & 1);
+            while (!got && clock64() - t0 < first_wait) got = mbar_test(&full_bar[s], (g / stages) & 1);
+          } else {
+            got = mbar_wait(&full_bar[s], (g / stages) & 1);
+          }
+          first = false;
+          if (!got) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = base_s + s * stage_bytes;
+          const uint32_t sb = sa + a_bytes;
+          const uint32_t sb2 = sb + b_bytes;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint64_t ad = desc_k_sw128(sa + kk * 32);
+            umma_bf16(d, ad, desc_k_sw128(sb + kk * 32), idesc, (kt | kk) != 0);
+            if (has_lo) umma_bf16(d, ad, desc_k_sw128(sb2 + kk * 32), idesc, 1u);
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull_bar[a]);
+      }
+      // every MMA of this CTA has completed once done_bar fires
+      umma_commit(&done_bar);
+      mbar_wait(&done_bar, 0);
+    }
+  } else {
+    // ---- epilogue (warps 2-5): TMEM lane quarter (warp % 4) -> rows
+    const int q = warp & 3;
+    const int row_in = q * 32 + lane;
+    int j = 0;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x, ++j) {
+      const int a = j & 1;
+      bool got = false;
+      {
+        const long long t0 = clock64();
+        const uint32_t par = (j >> 1) & 1;
+        while (!(got = mbar_test(&tfull_bar[a], par))) {
+          if (*(volatile int*)&failed || clock64() - t0 > TC_WAIT_CYCLES) break;
+        }
+      }
+      if (!got) {
+        fail();
         break;
       }
       tc_fence_after();
-      const uint32_t sa = base_s + s * stage_bytes;
-      const uint32_t sb = sa + a_bytes;
-      const uint32_t sb2 = sb + b_bytes;
+      const TcItem it = items[i];
+      const TcTask tk = tasks[it.task];
+      const int gm = it.mt * TC_BM + row_in;
+      float* const dst = tk.part ? tk.part + static_cast<int64_t>(it.kc) * tk.M * tk.ldp : tk.D;
+      const int64_t ldo = tk.part ? tk.ldp : tk.ldd;
+      const uint32_t src = tacc + static_cast<uint32_t>(a) * acc_cols + (static_cast<uint32_t>(q * 32) << 16);
+      float v[32];
+      for (int c0 = 0; c0 < bmax; c0 += 32) {
+        tmem_ld32(src + static_cast<uint32_t>(c0), v);
+        if (gm < tk.M) {
+          float* drow = dst + static_cast<int64_t>(gm) * ldo + c0;
+          if (c0 + 32 <= tk.N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        const uint64_t ad = desc_k_sw128(sa + kk * 32);
-        umma_bf16(tacc, ad, desc_k_sw128(sb + kk * 32), idesc, (kt | kk) != 0);
-        if (has_lo) umma_bf16(tacc, ad, desc_k_sw128(sb2 + kk * 32), idesc, 1u);
-      }
-      umma_commit(&empty_bar[s]);
-      ++mma_done;
-    }
-    umma_commit(&done_bar);
-  }
-  __syncthreads();
-
-  // epilogue: wait for the accumulator, then each warp reads its 32 lanes
-  bool ok = !*(volatile int*)&failed;
-  if (ok) ok = mbar_wait(&done_bar, 0);
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(&failed, 1);
-      atomicOr(err, 1);
-    }
-    // let in-flight copies and MMAs land before the shared memory and the
-    // tensor memory are released (bounded again)
-    if (warp == 0 && lane == 0)
-      for (int t = issued > stages ? issued - stages : 0; t < issued; ++t)
-        mbar_wait(&full_bar[t % stages], (t / stages) & 1);
-    if (tid == 32) mbar_wait(&done_bar, 0);
-  } else {
-    tc_fence_after();
-    const int row = warp * 32 + lane;
-    const int gm = it.mt * TC_BM + row;
-    // split-K chunks write their partial tile; the single chunk writes D
-    float* const dst = tk.part ? tk.part + static_cast<int64_t>(it.kc) * tk.M * tk.ldp : tk.D;
-    const int64_t ldo = tk.part ? tk.ldp : tk.ldd;
-    float v[32];
-    for (int c0 = 0; c0 < bmax; c0 += 32) {
-      tmem_ld32(tacc + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
-      if (gm < tk.M) {
-        float* drow = dst + static_cast<int64_t>(gm) * ldo + c0;
-        if (c0 + 32 <= tk.N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
+            for (int e = 0; e < 32; e += 4)
+              *reinterpret_cast<float4*>(drow + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(drow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < tk.N) drow[i] = v[i];
+            for (int e = 0; e < 32; ++e)
+              if (c0 + e < tk.N) drow[e] = v[e];
+          }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[a])) : "memory");
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tacc, ncols);
-  (void)mma_done;
 }
 
 // One CTA per (task, 16-row tile): rows x columns in float4 groups when the
@@ -381,7 +454,25 @@ cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* 
   const size_t bytes = tc_smem_bytes(stages, bmax);
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_tc_gemm<<<nitems, 128, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, stages, bmax, err);
+  // persistent: one CTA per SM (two TMEM accumulators of up to 256 columns
+  // take the whole tensor memory), at most one per item
+  static const int nsm = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return v > 0 ? v : 152;
+  }();
+  // test only: a short first wait (cycles) that exercises the timeout path
+  static const long long first_wait = [] {
+    const char* v = std::getenv("HSVD_TC_FIRST_WAIT_CYCLES");
+    return v ? std::atoll(v) : 0LL;
+  }();
+  const int grid = nitems < nsm ? nitems : nsm;
+  k_tc_gemm<<<grid, 192, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, nitems, stages, bmax, err,
+                                     first_wait);
   return cudaGetLastError();
 }
 

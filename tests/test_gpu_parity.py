@@ -11,6 +11,8 @@ Tolerances (stated per precision):
 The oracle consumes the same bytes as the GPU (BF16 inputs are rounded
 first), and uses the same rank tolerance, so rank decisions agree.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -21,6 +23,8 @@ from paper_1710_02812_gb300 import hsvd
 from paper_1710_02812_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+ROOT_REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 TOL = {"f64": (1e-10, 1e-6, 1.1e-16), "f32": (1e-4, 1e-3, 6e-8), "bf16_mixed": (1e-4, 1e-3, 6e-8)}
 RANK_TOL = {"f64": 1e-12, "f32": 1e-5, "bf16_mixed": 1e-5}
@@ -616,3 +620,38 @@ def test_autotune_picks_measured_variants_and_keeps_parity():
     check(xb, (u1, s1, v1), ref, "bf16_mixed", "autotuned", s_true=np.exp(-np.arange(300) / 20.0))
     st = plan.status()
     assert st["not_converged"] == 0 and st["nonfinite"] == 0 and st["tensor_timeouts"] == 0
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(tmp_path):
+    """The bounded waits of the tensor-core kernel: a test-only limit
+    (HSVD_TC_FIRST_WAIT_CYCLES, read once per process) makes the MMA issuer's
+    first wait give up before its tiles land; the kernel sets the error word,
+    waits (with the full limit) for its own copies and MMAs, frees its tensor
+    memory and returns.  Run in a child process: the run reports
+    tensor_timeouts > 0 and the CUDA context stays usable (a plain FP32 plan
+    afterwards matches the oracle)."""
+    import subprocess
+    import sys
+    code = f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {ROOT_REPO!r})
+from paper_1710_02812_gb300 import hsvd, workloads as W
+import oracle
+x = W.exp_decay(512, 512, r=100, noise=1e-5, tag=81, dtype=np.float32)
+xd = torch.from_numpy(x).cuda()
+p = hsvd.Plan(512, 512, 256, 256, "fixed_k", 16, prec="bf16_mixed", power_iters=1)
+p.run([xd])
+st = p.status()
+assert st["tensor_timeouts"] > 0, st
+q = hsvd.Plan(512, 512, 256, 256, "fixed_k", 16, prec="f32", power_iters=1)
+q.run([xd])
+u, s, v = q.factors(0)
+ref = oracle.hmat_svd(x.astype(np.float64), 256, 256, oracle.Rule("fixed_k", 16, rank_tol=1e-5))
+assert s.size == 16 and oracle.sigma_rel_err(s, ref.s, 4) <= 1e-4  # the context still computes
+torch.cuda.synchronize()
+print("ok", st["tensor_timeouts"])
+"""
+    env = dict(os.environ, HSVD_TC_FIRST_WAIT_CYCLES="1")
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-3000:]
+    assert p.stdout.strip().startswith("ok")
