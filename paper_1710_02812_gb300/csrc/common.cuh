@@ -162,6 +162,11 @@ constexpr int GEMM_SKINNY = 32;
 template <class TA>
 cudaError_t launch_gemm_tn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);
+// 128 x 128 tiles for large FP32 products (items address 128 x 128 tiles; no
+// split-K, second A segment or beta term).
+constexpr int GEMM_WIDE_TILE = 128;
+cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
+                             bool is_tn, const MatRef* mats, cudaStream_t s);
 template <class TA>
 cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);

@@ -594,6 +594,143 @@ __global__ void __launch_bounds__(128) k_gemm_nn_skinny(const GemmTask<TA, float
   }
 }
 
+// ---------------------------------------------------------------- v3 (FP32, wide tiles)
+// 128 x 128 CTA tiles for the large factor products (block-stage Grams and
+// R^-1 products, FP32-path input products): 256 threads each computing 8 x 8
+// outputs (rows 8 ty .. 8 ty + 7, columns 4 tx .. 4 tx + 3 and 64 + 4 tx ..),
+// four 16-byte shared loads per 64 FMAs instead of three per 32; BK = 16 with
+// the next K tile loaded into registers while the current one is used.  No
+// split-K, no second A segment and no beta term (the caller only routes
+// products without them here); C = alpha A B or alpha A^T B.
+constexpr int BM3 = 128, BN3 = 128, BK3 = 16;
+
+template <bool IS_TN>
+__global__ void __launch_bounds__(256, 2) k_gemm3(const GemmTask<float, float, float>* __restrict__ tasks,
+                                               const GemmItem* __restrict__ items, const MatRef* __restrict__ mats) {
+  __shared__ __align__(16) float As[2][BK3][BM3 + 4];
+  __shared__ __align__(16) float Bs[2][BK3][BN3 + 4];
+  const GemmItem it = items[blockIdx.x];
+  const GemmTask<float, float, float>& tk = tasks[it.task];
+  const int M = eff(tk.M), N = eff(tk.N), K = eff(tk.K);
+  const int m0 = it.mt * BM3, n0 = it.nt * BN3;
+  if (m0 >= M || n0 >= N) return;
+  int ke = K;
+  if (!IS_TN && tk.btri) ke = min(ke, n0 + BN3);  // B upper triangular
+  const float* A = tk.A;
+  int64_t lda = tk.lda;
+  if (tk.mat >= 0) {
+    const MatRef mr = mats[tk.mat];
+    A = static_cast<const float*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
+    lda = mr.ld;
+  }
+  const float* B = tk.B;
+  const int64_t ldb = tk.ldb;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const bool avec = aligned16(A, lda);
+  const bool bvec = aligned16(B, ldb);
+
+  float ra[8], rb[8];
+  auto load_tiles = [&](int k0) {
+    if (!IS_TN) {  // A tile: 128 rows x 16 k, thread -> row tid >> 1, k (tid & 1) * 8
+      const int r = tid >> 1, kk = (tid & 1) * 8;
+      const int gm = m0 + r, gk = k0 + kk;
+      if (avec && gm < M && gk + 8 <= ke) {
+        load8(A + (int64_t)gm * lda + gk, ra);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ra[i] = (gm < M && gk + i < ke) ? A[(int64_t)gm * lda + gk + i] : 0.f;
+      }
+    } else {  // A tile: 16 k x 128 m, thread -> k tid >> 4, m (tid & 15) * 8
+      const int kk = tid >> 4, mm = (tid & 15) * 8;
+      const int gk = k0 + kk, gm = m0 + mm;
+      if (avec && gk < ke && gm + 8 <= M) {
+        load8(A + (int64_t)gk * lda + gm, ra);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ra[i] = (gk < ke && gm + i < M) ? A[(int64_t)gk * lda + gm + i] : 0.f;
+      }
+    }
+    {  // B tile: 16 k x 128 n, thread -> k tid >> 4, n (tid & 15) * 8
+      const int kk = tid >> 4, nn = (tid & 15) * 8;
+      const int gk = k0 + kk, gn = n0 + nn;
+      if (bvec && gk < ke && gn + 8 <= N) {
+        load8(B + (int64_t)gk * ldb + gn, rb);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) rb[i] = (gk < ke && gn + i < N) ? B[(int64_t)gk * ldb + gn + i] : 0.f;
+      }
+    }
+  };
+  auto store_tiles = [&](int buf) {
+    if (!IS_TN) {
+      const int r = tid >> 1, kk = (tid & 1) * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[buf][kk + i][r] = ra[i];
+    } else {
+      const int kk = tid >> 4, mm = (tid & 15) * 8;
+      *reinterpret_cast<float4*>(&As[buf][kk][mm]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+      *reinterpret_cast<float4*>(&As[buf][kk][mm + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+    }
+    const int kk = tid >> 4, nn = (tid & 15) * 8;
+    *reinterpret_cast<float4*>(&Bs[buf][kk][nn]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4*>(&Bs[buf][kk][nn + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (ke > 0) {
+    load_tiles(0);
+    store_tiles(0);
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < ke; k0 += BK3) {
+    const bool more = k0 + BK3 < ke;
+    if (more) load_tiles(k0 + BK3);
+#pragma unroll
+    for (int kk = 0; kk < BK3; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) store_tiles(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+
+  const float alpha = tk.alpha;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + ty * 8 + i;
+    if (gm >= M) continue;
+    float* crow = tk.C + (int64_t)gm * tk.ldc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gn = n0 + h * 64 + tx * 4;
+      if (gn + 4 <= N && ((reinterpret_cast<uintptr_t>(crow + gn) & 15) == 0)) {
+        *reinterpret_cast<float4*>(crow + gn) = make_float4(alpha * acc[i][4 * h], alpha * acc[i][4 * h + 1],
+                                                            alpha * acc[i][4 * h + 2], alpha * acc[i][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (gn + j < N) crow[gn + j] = alpha * acc[i][4 * h + j];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <class TA, class TB, class TC>
@@ -626,6 +763,16 @@ cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem
     k_gemm2_reduce<TA><<<nitems, 256, 0, s>>>(tasks, items);
   else
     k_gemm_reduce<TA, TB, TC><<<nitems, NT, 0, s>>>(tasks, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
+                             bool is_tn, const MatRef* mats, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (is_tn)
+    k_gemm3<true><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else
+    k_gemm3<false><<<nitems, 256, 0, s>>>(tasks, items, mats);
   return cudaGetLastError();
 }
 

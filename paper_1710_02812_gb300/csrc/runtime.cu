@@ -411,9 +411,60 @@ struct Builder {
     }
   }
 
+  // Large FP32 products (no second A segment, no beta term, at least 128
+  // output rows and columns, enough 128 x 128 tiles to fill the GPU twice)
+  // run on 128 x 128 tiles without split-K.  HSVD_NO_WIDE turns this off.
+  template <class G>
+  bool emit_gemm_wide(const std::string& name, std::vector<G>& tasks, bool is_tn) {
+    using TAx = typename TaOf<G>::type;
+    if constexpr (!std::is_same<T, float>::value || !std::is_same<TAx, float>::value) {
+      return false;
+    } else {
+      static const bool off = std::getenv("HSVD_NO_WIDE") != nullptr;
+      if (off) return false;
+      constexpr int W = GEMM_WIDE_TILE;
+      int64_t tiles = 0;
+      int ncols = 0;
+      for (const auto& g : tasks) {
+        if (g.A2 || g.C0 || g.K.cap > 8192) return false;
+        if (g.M.cap < W || g.N.cap < W) return false;
+        for (int mt = 0; mt < cdiv(g.M.cap, W); ++mt)
+          for (int nt = 0; nt < cdiv(g.N.cap, W); ++nt) tiles += (g.sym && nt < mt) ? 0 : 1;
+        ncols = std::max(ncols, g.N.cap);
+      }
+      if (tiles < 2 * (int64_t)num_sms()) return false;
+      std::vector<GemmItem> items;
+      for (size_t t = 0; t < tasks.size(); ++t) {
+        G& g = tasks[t];
+        g.mtiles = cdiv(g.M.cap, W);
+        g.ntiles = cdiv(g.N.cap, W);
+        g.nkc = 1;
+        g.kchunk = 0;
+        g.partial = nullptr;
+        for (int mt = 0; mt < g.mtiles; ++mt)
+          for (int nt = 0; nt < g.ntiles; ++nt)
+            if (!(g.sym && nt < mt)) items.push_back(GemmItem{(int)t, mt, nt, 0});
+      }
+      double gfl, gby;
+      int gcols;
+      gemm_work(tasks, is_tn, gfl, gby, gcols);
+      PlanImpl* p = &P;
+      const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
+      const int ni = (int)items.size();
+      P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn](cudaStream_t s) {
+                               return launch_gemm_wide(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn,
+                                                       p->d_mats, s);
+                             }});
+      tag(is_tn ? 2 : 1, (int)tasks.size(), gcols, gfl, gby);
+      (void)ncols;
+      return true;
+    }
+  }
+
   template <class G>
   void emit_gemm(const std::string& name, std::vector<G> tasks, bool is_tn) {
     if (tasks.empty()) return;
+    if (emit_gemm_wide(name, tasks, is_tn)) return;
     std::vector<GemmItem> items, red;
     finish_items(tasks, is_tn, items, red);
     if (items.empty()) return;
