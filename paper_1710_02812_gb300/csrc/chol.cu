@@ -450,19 +450,20 @@ __global__ void __launch_bounds__(256) k_chol_reg(const CholTask<T>* __restrict_
 //     Rh[J, C] = Rh[J, J]^{-T} Gh[J, C] by forward substitution (lane =
 //     column); the trailing tiles Gh[I, C] -= Rh[J, I]^T Rh[J, C], each a
 //     32 x 32 x 32 product with an 8 x 4 register tile per lane.
-//   inverse, bottom-up by block rows I: X[I, I] = Rh[I, I]^{-1} (one warp,
-//     back substitution, lane = column) while other warps form
-//     T_J = sum_{I < L <= J} Rh[I, L] X[L, J]; then X[I, J] = -X[I, I] T_J,
+//   inverse: every diagonal tile X[I, I] = Rh[I, I]^{-1} first (a warp each,
+//     back substitution, lane = column), then bottom-up by block rows I:
+//     T_J = sum_{I < L <= J} Rh[I, L] X[L, J] and X[I, J] = -X[I, I] T_J,
 //     written over Rh[I, J] (row block I of Rh is not read again).
-// Three CTA barriers per block column or block row instead of one per
-// column of the elimination.
+// Two CTA barriers per block column or block row instead of one per column
+// of the elimination; the diagonal tiles are factored ahead (during the
+// previous block column's trailing update) and inverted all at once.
 constexpr int CB_LD = 36;
 constexpr int CB_TS = 32 * CB_LD;
 constexpr int CB_NT = 8;
 constexpr int CB_NUP = CB_NT * (CB_NT + 1) / 2;
 constexpr int CB_THREADS = 256;
 constexpr int CB_NW = CB_THREADS / 32;
-constexpr size_t CB_SMEM = (size_t)(CB_NUP + CB_NT + 1) * CB_TS * sizeof(float);
+constexpr size_t CB_SMEM = (size_t)(CB_NUP + CB_NT) * CB_TS * sizeof(float);
 
 __device__ __forceinline__ int cb_tile(int I, int J, int nt) { return I * nt - I * (I - 1) / 2 + (J - I); }
 
@@ -473,7 +474,6 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* __restrict__ tiles = reinterpret_cast<float*>(smem_raw);
   float* __restrict__ temps = tiles + CB_NUP * CB_TS;
-  float* __restrict__ xdiag = temps + CB_NT * CB_TS;
   __shared__ float sc[32 * CB_NT];
   __shared__ int bad, ndrop;
   const CholTask<float>& tk = tasks[blockIdx.x];
@@ -523,36 +523,42 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
   __syncthreads();
 
   // ---------------------------------------------------------------- factor
-  for (int J = 0; J < nt; ++J) {
+  // Diagonal tile J (one warp, lane c keeps column c): Rh[J, J] with pivot
+  // dropping.  Tile 0 first; tile J + 1 is factored by the warp that applies
+  // its last trailing update, inside step J (look-ahead), so only the panel
+  // and the trailing update wait at the step's barriers.
+  auto factor_diag = [&](int J) {
     float* D = tiles + cb_tile(J, J, nt) * CB_TS;
-    if (warp == 0) {
-      float col[32];
+    float col[32];
 #pragma unroll
-      for (int r = 0; r < 32; ++r) col[r] = D[r * CB_LD + lane];
-      int nd = 0;
+    for (int r = 0; r < 32; ++r) col[r] = D[r * CB_LD + lane];
+    int nd = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float d = __shfl_sync(FULL, col[j], j);
-        const int gj = 32 * J + j;
-        const bool pad = gj >= k;
-        const bool drop = pad || !(sc[gj] > 0.f) || !(d > tau);
-        if (drop && !pad) ++nd;
-        const float rinv = drop ? 0.f : 1.f / sqrtf(d);
-        const float rj = lane >= j ? col[j] * rinv : 0.f;
-        col[j] = rj;
+    for (int j = 0; j < 32; ++j) {
+      const float d = __shfl_sync(FULL, col[j], j);
+      const int gj = 32 * J + j;
+      const bool pad = gj >= k;
+      const bool drop = pad || !(sc[gj] > 0.f) || !(d > tau);
+      if (drop && !pad) ++nd;
+      const float rinv = drop ? 0.f : 1.f / sqrtf(d);
+      const float rj = lane >= j ? col[j] * rinv : 0.f;
+      col[j] = rj;
 #pragma unroll
-        for (int i = 1; i < 32; ++i) {
-          if (i > j) {  // resolved at compile time: both loops are unrolled
-            const float ri = __shfl_sync(FULL, rj, i);
-            if (lane >= i) col[i] = fmaf(-ri, rj, col[i]);
-          }
+      for (int i = 1; i < 32; ++i) {
+        if (i > j) {  // resolved at compile time: both loops are unrolled
+          const float ri = __shfl_sync(FULL, rj, i);
+          if (lane >= i) col[i] = fmaf(-ri, rj, col[i]);
         }
       }
-#pragma unroll
-      for (int r = 0; r < 32; ++r) D[r * CB_LD + lane] = lane >= r ? col[r] : 0.f;
-      if (lane == 0 && nd) ndrop += nd;
     }
-    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) D[r * CB_LD + lane] = lane >= r ? col[r] : 0.f;
+    if (lane == 0 && nd) atomicAdd(&ndrop, nd);
+  };
+  if (warp == 0) factor_diag(0);
+  __syncthreads();
+  for (int J = 0; J < nt; ++J) {
+    const float* D = tiles + cb_tile(J, J, nt) * CB_TS;
     // panel: solve Rh[J,J]^T X = Gh[J, C] for every C > J (lane = column)
     for (int C = J + 1 + warp; C < nt; C += CB_NW) {
       float* B = tiles + cb_tile(J, C, nt) * CB_TS;
@@ -576,6 +582,7 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
       const int m = nt - J - 1;
       const int ntask = m * (m + 1) / 2;
       const int ri = lane >> 3, ci = lane & 7;
+      // task 0 is tile (J + 1, J + 1), warp 0's first: its last update
       for (int task = warp; task < ntask; task += CB_NW) {
         int I = J + 1, rem = task;
         while (rem >= nt - I) {
@@ -612,6 +619,10 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
           w.w -= acc[u][3];
           *o = w;
         }
+        if (task == 0) {  // the next diagonal tile is final: factor it now
+          __syncwarp();
+          factor_diag(J + 1);
+        }
       }
     }
     __syncthreads();
@@ -630,30 +641,37 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
   if (!tk.Rinv) return;
 
   // ---------------------------------------------------------------- inverse
-  for (int I = nt - 1; I >= 0; --I) {
-    const float* D = tiles + cb_tile(I, I, nt) * CB_TS;
-    if (warp == 0) {
-      // X[I, I] = D^{-1}: column c by back substitution
-      float x[32];
-      const float dcc = D[lane * CB_LD + lane];
+  // Every diagonal tile first, in place and in parallel (warp w inverts
+  // tile w: X[I, I] = Rh[I, I]^{-1}, column c by back substitution); then
+  // bottom-up by block rows: T_J = sum_{I < L <= J} Rh[I, L] X[L, J] and
+  // X[I, J] = -X[I, I] T_J over Rh[I, J].
+  __syncthreads();  // the R output above has read the diagonal tiles
+  for (int I = warp; I < nt; I += CB_NW) {
+    float* D = tiles + cb_tile(I, I, nt) * CB_TS;
+    float x[32];
+    const float dcc = D[lane * CB_LD + lane];
 #pragma unroll
-      for (int r = 0; r < 32; ++r) x[r] = 0.f;
+    for (int r = 0; r < 32; ++r) x[r] = 0.f;
 #pragma unroll
-      for (int r = 31; r >= 0; --r) {
-        float acc = r == lane ? 1.f : 0.f;
+    for (int r = 31; r >= 0; --r) {
+      float acc = r == lane ? 1.f : 0.f;
 #pragma unroll
-        for (int l = r + 1; l < 32; ++l) acc = fmaf(-D[r * CB_LD + l], x[l], acc);
-        const float drr = D[r * CB_LD + r];
-        x[r] = (r <= lane && drr > 0.f && dcc > 0.f) ? acc / drr : 0.f;
-      }
+      for (int l = r + 1; l < 32; ++l) acc = fmaf(-D[r * CB_LD + l], x[l], acc);
+      const float drr = D[r * CB_LD + r];
+      x[r] = (r <= lane && drr > 0.f && dcc > 0.f) ? acc / drr : 0.f;
+    }
+    __syncwarp();  // every lane has read the tile before it is overwritten
 #pragma unroll
-      for (int r = 0; r < 32; ++r) xdiag[r * CB_LD + lane] = x[r];
-    } else {
-      // T_J = sum_{I < L <= J} Rh[I, L] X[L, J]: task (J, half h), 16 rows
-      // 16 h + ri + 4 u (u < 4) and columns 4 ci .. 4 ci + 3 per lane
+    for (int r = 0; r < 32; ++r) D[r * CB_LD + lane] = x[r];
+  }
+  __syncthreads();
+  for (int I = nt - 2; I >= 0; --I) {
+    {
+      // T_J: task (J, half h), 16 rows 16 h + ri + 4 u (u < 4) and columns
+      // 4 ci .. 4 ci + 3 per lane
       const int ri = lane >> 3, ci = lane & 7;
       const int ntask = 2 * (nt - 1 - I);
-      for (int task = warp - 1; task < ntask; task += CB_NW - 1) {
+      for (int task = warp; task < ntask; task += CB_NW) {
         const int J = I + 1 + (task >> 1), h = task & 1;
         float acc[4][4];
 #pragma unroll
@@ -691,20 +709,13 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
       }
     }
     __syncthreads();
-    // X[I, J] = -X[I, I] T_J over Rh[I, J]; X[I, I] copied over Rh[I, I].
-    // Rows ri + 4 u (u < 8) and columns 4 ci .. 4 ci + 3 per lane.
+    // X[I, J] = -X[I, I] T_J over Rh[I, J], J > I: rows ri + 4 u (u < 8) and
+    // columns 4 ci .. 4 ci + 3 per lane
     {
       const int ri = lane >> 3, ci = lane & 7;
-      for (int J = I + warp; J < nt; J += CB_NW) {
+      const float* X = tiles + cb_tile(I, I, nt) * CB_TS;
+      for (int J = I + 1 + warp; J < nt; J += CB_NW) {
         float* O = tiles + cb_tile(I, J, nt) * CB_TS;
-        if (J == I) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int r = ri + 4 * u;
-            *reinterpret_cast<float4*>(O + r * CB_LD + ci * 4) = ld4(xdiag + r * CB_LD + ci * 4);
-          }
-          continue;
-        }
         const float* T = temps + (J - I - 1) * CB_TS;
         float acc[8][4];
 #pragma unroll
@@ -718,7 +729,7 @@ __global__ void __launch_bounds__(CB_THREADS, 1) k_chol_wide(const CholTask<floa
           for (int q = 0; q < 4; ++q) b[q] = ld4(T + (mm + q) * CB_LD + ci * 4);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float4 a = ld4(xdiag + (ri + 4 * u) * CB_LD + mm);
+            const float4 a = ld4(X + (ri + 4 * u) * CB_LD + mm);
             const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
