@@ -397,6 +397,21 @@ int32_t hsvd_tree_levels(int64_t count);
  * EINVAL otherwise.  Exposed so the ordering can be checked without a GPU. */
 hsvd_status hsvd_jacobi_pair(int32_t n, int32_t round, int32_t slot, int32_t* p, int32_t* q);
 
+/* hsvd_jacobi_block_order -- host-only: the ordering of the FP32 cores of
+ * 129..256 columns held in registers (a cluster of two CTAs, each with 128
+ * column slots in 16 blocks of 8 held two per warp by 8 warps).
+ *   what 0: blocks (*a, *b) held by warp `j` in round `i` of phase `phase`
+ *           (phase 0: 0 <= i < 15, the CTA's own blocks; phases 1 and 2:
+ *           0 <= i < 8, after the first and second exchange of a quarter
+ *           with the other CTA);
+ *   what 1: register columns (*a, *b) (0..7 first block, 8..15 second) of
+ *           pair j (0 <= j < 8) in step i of kind `phase` (0: the two blocks
+ *           against each other, 0 <= i < 8; 1: inside each block, 0 <= i < 7).
+ * Returns 0, or EINVAL for arguments out of range or null pointers.  Exposed
+ * so that the coverage of every column pair once per sweep can be checked
+ * without a GPU. */
+hsvd_status hsvd_jacobi_block_order(int32_t what, int32_t phase, int32_t i, int32_t j, int32_t* a, int32_t* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -179,7 +179,17 @@ template <class T>
 cudaError_t launch_chol(const CholTask<T>* tasks, int ntasks, int kcap, DevStatus* st, double tau,
                         cudaStream_t s, bool with_product);
 // Kernels of a core launch (autotuning); JV_AUTO is the default dispatch.
-enum { JV_AUTO = 0, JV_BP1 = 1, JV_BP2 = 2, JV_SPLIT = 3, JV_CLUSTER = 4, JV_SM4 = 5, JV_SM8 = 6, JV_SM16 = 7 };
+enum {
+  JV_AUTO = 0,
+  JV_BP1 = 1,
+  JV_BP2 = 2,
+  JV_SPLIT = 3,
+  JV_CLUSTER = 4,
+  JV_SM4 = 5,
+  JV_SM8 = 6,
+  JV_SM16 = 7,
+  JV_REG = 8
+};
 template <class T>
 cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                           TruncParams tp, DevStatus* st, cudaStream_t s, int variant = JV_AUTO);
@@ -308,6 +318,15 @@ cudaError_t launch_jacobi_split(const JacobiTask<float>* tasks, int ntasks, int 
                                 TruncParams tp, DevStatus* st, cudaStream_t s, bool* done);
 cudaError_t launch_jacobi_bp(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
                              TruncParams tp, DevStatus* st, cudaStream_t s, bool* done, int force_minb);
+// The FP32 register-resident cluster kernel (129..256 columns, at most 256
+// rows, no accumulated rotations; *done false: not launched).  forced: run
+// even when HSVD_JACOBI_REG=0 takes it out of the default dispatch.
+bool jacobi_reg_fits(int nrcap, int nccap, bool want_v);
+cudaError_t launch_jacobi_reg(const JacobiTask<float>* tasks, int ntasks, int nrcap, int nccap, bool want_v,
+                              TruncParams tp, DevStatus* st, cudaStream_t s, bool* done, bool forced);
+// Its block schedule and step pairs, for checks without a GPU.
+void jacobi_rr_sched_host(int ph, int r, int w, int* a, int* b);
+void jacobi_rr_pair_host(int kind, int step, int pair, int* i, int* j);
 size_t jacobi_work_bytes(int nrcap, int nccap, bool want_v, size_t elem);
 bool chol_uses_smem(int kcap, size_t elem);
 

@@ -585,6 +585,8 @@ cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int
         e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, variant == JV_BP1 ? 1 : 2);
       else if (variant == JV_SPLIT)
         e = launch_jacobi_split(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
+      else if (variant == JV_REG)
+        e = launch_jacobi_reg(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, true);
       else if (variant == JV_CLUSTER)
         e = launch_jacobi_cluster(tasks, ntasks, nrcap, nccap, want_v, 2, tp, st, s, &done);
     }
@@ -600,7 +602,10 @@ cudaError_t launch_jacobi(const JacobiTask<T>* tasks, int ntasks, int nrcap, int
     e = launch_jacobi_bp(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, 0);
     if (e != cudaSuccess || done) return e;
     // Cores one CTA cannot hold are spread over a cluster: by columns (two
-    // CTAs, columns exchanged twice per sweep), else by rows.
+    // CTAs, columns exchanged twice per sweep; held in registers, else in
+    // shared memory), else by rows.
+    e = launch_jacobi_reg(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done, false);
+    if (e != cudaSuccess || done) return e;
     e = launch_jacobi_split(tasks, ntasks, nrcap, nccap, want_v, tp, st, s, &done);
     if (e != cudaSuccess || done) return e;
     const int C = jacobi_cluster_size(ntasks, nrcap, nccap, !jacobi_sm_fits(nrcap, nccap, want_v, sizeof(T)));
@@ -639,6 +644,7 @@ std::vector<int> jacobi_variants(int nrcap, int nccap, bool want_v, size_t elem)
       v.push_back(JV_BP1);
       if (jacobi_bp_two_per_sm(nrcap, nccap, want_v)) v.push_back(JV_BP2);
     }
+    if (jacobi_reg_fits(nrcap, nccap, want_v)) v.push_back(JV_REG);
     if (!want_v && nccap > 128 && nccap <= 256 && nrcap <= 256) v.push_back(JV_SPLIT);
     if (nccap > 128 && nccap <= 256 && nrcap <= 256 && jacobi_cluster_smem(nrcap, nccap, want_v, 2) > 0 &&
         jacobi_cluster_smem(nrcap, nccap, want_v, 2) <= 200 * 1024)
@@ -661,6 +667,7 @@ const char* jacobi_variant_name(int v) {
     case JV_BP1: return "jacobi:block-pair, 1 CTA/SM";
     case JV_BP2: return "jacobi:block-pair, 2 CTAs/SM";
     case JV_SPLIT: return "jacobi:column-split cluster";
+    case JV_REG: return "jacobi:column-split cluster, registers";
     case JV_CLUSTER: return "jacobi:row-split cluster";
     case JV_SM4: return "jacobi:shared memory, 4 lanes/pair";
     case JV_SM8: return "jacobi:shared memory, 8 lanes/pair";

@@ -33,6 +33,7 @@
 #include "common.cuh"
 #include "jacobi.cuh"
 #include "jacobi_bp.cuh"
+#include "jacobi_cs.cuh"
 
 namespace hsvd {
 
@@ -104,44 +105,18 @@ __global__ void __launch_bounds__(CS_THREADS, 1) k_jacobi_cs(const JacobiTask<fl
   __shared__ float nrm[CS_NL];
   __shared__ float sig_s[2 * CS_NL];
   __shared__ int perm[2 * CS_NL];
+  __shared__ float inv_s[2 * CS_NL];
   __shared__ int vote[2];
   __shared__ int rank_s;
   const int me = static_cast<int>(cl_rank());
   const uint32_t peer = static_cast<uint32_t>(me ^ 1);
   const JacobiTask<float>& tk = tasks[blockIdx.x >> 1];
-  int nr, nc, k1 = 0, k2 = 0;
-  if (tk.load == 1) {
-    k1 = eff(tk.k1);
-    k2 = eff(tk.k2);
-    nr = nc = k1 + k2;
-  } else {
-    nr = eff(tk.nr);
-    nc = eff(tk.nc);
-  }
+  int nr, nc, k1, k2;
+  cs_dims(tk, nr, nc, k1, k2);
   const int tid = threadIdx.x;
-  const int col0 = me * CS_NL;
 
-  // ---- this CTA's columns col0 .. col0 + 127 (merge cores: E itself)
-  for (int e = tid; e < CS_ROWS * CS_NL; e += CS_THREADS) {
-    const int i = e % CS_ROWS, j = e / CS_ROWS, gj = col0 + j;
-    float v = 0.f;
-    if (gj < nc && i < nr) {
-      if (tk.load == 0) {
-        v = tk.src[(int64_t)i * tk.rs + (int64_t)gj * tk.cs];
-      } else if (i < k1) {
-        if (gj < k1) {
-          v = (i == gj) ? tk.s1[i] : 0.f;
-        } else {
-          float p = tk.P[(int64_t)i * tk.ldp + (gj - k1)];
-          if (tk.P2) p += tk.P2[(int64_t)i * tk.ldp + (gj - k1)];
-          v = p * tk.s2[gj - k1];
-        }
-      } else if (gj >= k1) {
-        v = tk.R[(int64_t)(i - k1) * tk.ldr + (gj - k1)] * tk.s2[gj - k1];
-      }
-    }
-    Mw[j * CS_LDM + i] = v;
-  }
+  // ---- this CTA's columns me * 128 .. me * 128 + 127 (merge cores: E itself)
+  cs_load_core<CS_THREADS, CS_LDM>(tk, Mw, me, nr, nc, k1);
   if (tid < 2) vote[tid] = 0;
   // every CTA of the cluster has started before any peer store
   cl_sync();
@@ -210,93 +185,8 @@ __global__ void __launch_bounds__(CS_THREADS, 1) k_jacobi_cs(const JacobiTask<fl
     atomicAdd(&st->cores, 1);
   }
 
-  // ---- column norms of all 256 slots in both CTAs (slot index me * 128 + j)
-  for (int j = tid >> 3; j < CS_NL; j += CS_THREADS >> 3) {
-    const float* x = Mw + j * CS_LDM;
-    float a = 0.f;
-    for (int i = lane; i < nr; i += 8) a = fmaf(x[i], x[i], a);
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) a += __shfl_xor_sync(gm8, a, off);
-    if (lane == 0) {
-      const float sv = isfinite(a) ? sqrtf(a) : -1.f;
-      sig_s[col0 + j] = sv;
-      cl_st(cl_addr(&sig_s[col0 + j], peer), sv);
-    }
-  }
-  cl_sync();
-  // ---- sort (identical in both CTAs), rank rule, outputs
-  const int ns = 2 * CS_NL;
-  for (int j = tid; j < ns; j += CS_THREADS) {
-    const float sj = sig_s[j];
-    int pos = 0;
-    for (int i = 0; i < ns; ++i) {
-      const float si = sig_s[i];
-      pos += (si > sj) || (si == sj && i < j);
-    }
-    perm[pos] = j;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int bad = 0;
-    for (int i = 0; i < ns; ++i) bad += sig_s[i] < 0.f;
-    if (bad && st && me == 0) atomicAdd(&st->nonfinite, 1);
-    int r = 0;
-    const double s1 = (double)sig_s[perm[0]];
-    if (s1 > 0.0 && !bad) {
-      int numerical = 0;
-      for (int i = 0; i < ns; ++i) numerical += (double)sig_s[perm[i]] > tp.rank_tol * s1;
-      if (tp.mode == 0) {
-        r = (int)tp.param;
-      } else if (tp.mode == 1) {
-        for (int i = 0; i < ns; ++i) r += (double)sig_s[perm[i]] >= tp.param * s1;
-      } else {
-        double total = 0.0;
-        if (tk.energy) {
-          total = (double)*tk.energy;
-        } else if (tk.load == 1) {
-          for (int i = 0; i < k1; ++i) total += (double)tk.s1[i] * (double)tk.s1[i];
-          for (int i = 0; i < k2; ++i) total += (double)tk.s2[i] * (double)tk.s2[i];
-        } else {
-          for (int i = 0; i < ns; ++i) total += (double)sig_s[i] * (double)sig_s[i];
-        }
-        double cum = 0.0;
-        r = nc;
-        for (int i = 0; i < ns; ++i) {
-          const double sv = (double)sig_s[perm[i]];
-          cum += sv * sv;
-          if (cum >= tp.param * total) {
-            r = i + 1;
-            break;
-          }
-        }
-      }
-      r = min(r, numerical);
-      r = min(r, tp.rank_cap);
-      r = min(r, nc);
-      r = min(r, tk.ucap);
-      if (r < 0) r = 0;
-    }
-    rank_s = r;
-    if (me == 0 && tk.rank) *tk.rank = r;
-  }
-  __syncthreads();
-  const int r = rank_s;
-  if (me == 0 && tk.sig)
-    for (int c = tid; c < tk.ucap; c += CS_THREADS) tk.sig[c] = (c < r) ? sig_s[perm[c]] : 0.f;
-  if (tk.U) {
-    // output column c comes from the CTA holding slot perm[c]; CTA 0 also
-    // writes the zero columns past the rank
-    for (int e = tid; e < nr * tk.ucap; e += CS_THREADS) {
-      const int i = e / tk.ucap, c = e % tk.ucap;
-      if (c < r) {
-        const int sl = perm[c];
-        if ((sl >> 7) == me) tk.U[(int64_t)i * tk.ldu + c] = Mw[(sl & 127) * CS_LDM + i] / sig_s[sl];
-      } else if (me == 0) {
-        tk.U[(int64_t)i * tk.ldu + c] = 0.f;
-      }
-    }
-  }
-  cl_sync();  // no CTA leaves while its peer may still address its shared memory
+  cs_norms_exchange<CS_THREADS, CS_LDM>(Mw, me, peer, nr, sig_s);
+  cs_finish<CS_THREADS, CS_LDM>(tk, Mw, me, nr, nc, k1, k2, tp, st, sig_s, perm, inv_s, &rank_s);
 }
 
 bool split_enabled() {

@@ -1722,6 +1722,23 @@ hsvd_status hsvd_jacobi_pair(int32_t n, int32_t round, int32_t slot, int32_t* p,
   return HSVD_OK;
 }
 
+hsvd_status hsvd_jacobi_block_order(int32_t what, int32_t phase, int32_t i, int32_t j, int32_t* a, int32_t* b) {
+  if (!a || !b) return HSVD_EINVAL;
+  int aa = 0, bb = 0;
+  if (what == 0) {
+    if (phase < 0 || phase > 2 || i < 0 || i >= (phase == 0 ? 15 : 8) || j < 0 || j >= 8) return HSVD_EINVAL;
+    hsvd::jacobi_rr_sched_host(phase, i, j, &aa, &bb);
+  } else if (what == 1) {
+    if (phase < 0 || phase > 1 || i < 0 || i >= (phase == 0 ? 8 : 7) || j < 0 || j >= 8) return HSVD_EINVAL;
+    hsvd::jacobi_rr_pair_host(phase, i, j, &aa, &bb);
+  } else {
+    return HSVD_EINVAL;
+  }
+  *a = aa;
+  *b = bb;
+  return HSVD_OK;
+}
+
 hsvd_status hsvd_plan(hsvd_plan_t* out, int32_t batch, const int64_t* m, const int64_t* n, int64_t block_rows,
                       int64_t block_cols, hsvd_trunc mode, double param, int32_t rank_cap, hsvd_tree tree,
                       hsvd_prec prec, hsvd_dtype in_dtype, const hsvd_options* opts) {

@@ -29,7 +29,7 @@ EXPORTED = ("hsvd_plan", "hsvd_run", "hsvd_run_host", "hsvd_status_query", "hsvd
             "hsvd_set_timing", "hsvd_step_times", "hsvd_block_svd_noalloc", "hsvd_last_error",
             "hsvd_refine", "hsvd_gram", "hsvd_tree_root", "hsvd_merge_plan", "hsvd_merge_run",
             "hsvd_recover_begin", "hsvd_recover_orth", "hsvd_recover_core", "hsvd_recover_signs",
-            "hsvd_recover_finish", "hsvd_step_variant")
+            "hsvd_recover_finish", "hsvd_step_variant", "hsvd_jacobi_block_order")
 STEP_KIND = {1: "gemm_nn", 2: "gemm_tn", 3: "gemm_reduce", 4: "chol", 5: "jacobi", 6: "energy", 7: "signs",
              8: "gemm_tc", 9: "convert"}
 
@@ -94,6 +94,8 @@ def lib():
         L.hsvd_tree_levels.restype = i32
         L.hsvd_jacobi_pair.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hsvd_jacobi_pair.restype = ctypes.c_int
+        L.hsvd_jacobi_block_order.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.hsvd_jacobi_block_order.restype = ctypes.c_int
         L.hsvd_step_count.argtypes = [P]
         L.hsvd_step_count.restype = i32
         L.hsvd_step_info.argtypes = [P, i32, ctypes.c_char_p, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -342,6 +344,14 @@ def hsvd_jacobi_pair(n: int, rnd: int, slot: int):
     if code != HSVD_OK:
         raise HsvdError(code, "hsvd_jacobi_pair")
     return p.value, q.value
+
+
+def hsvd_jacobi_block_order(what: int, phase: int, i: int, j: int):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    code = lib().hsvd_jacobi_block_order(what, phase, i, j, ctypes.byref(a), ctypes.byref(b))
+    if code != HSVD_OK:
+        raise HsvdError(code, "hsvd_jacobi_block_order")
+    return a.value, b.value
 
 
 def check_noalloc_args(A, m, n, k, U, S, rank, flags=None, lda=None, ldu=None, require_cuda=True) -> None:

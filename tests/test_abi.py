@@ -65,6 +65,65 @@ def test_jacobi_round_robin_covers_each_pair_once(lib, n):
     assert len(seen) == n * (n - 1) // 2
 
 
+def test_register_core_ordering_covers_each_column_pair_once_per_sweep(lib):
+    """The ordering of the register-resident cluster cores: two CTAs of 16
+    blocks of 8 columns, 15 + 8 + 8 rounds and two exchanges of a quarter per
+    sweep.  Every pair of the 256 columns meets exactly once; in every round
+    the 8 warps of a CTA hold its 16 blocks once each; the 8 pairs of a step
+    use 16 distinct register columns."""
+    order = hsvd.hsvd_jacobi_block_order
+    for kind, nsteps in ((0, 8), (1, 7)):
+        seen = set()
+        for t in range(nsteps):
+            cols = [c for p in range(8) for c in order(1, kind, t, p)]
+            assert sorted(cols) == list(range(16))
+            for p in range(8):
+                a, b = order(1, kind, t, p)
+                if kind == 0:
+                    assert a < 8 <= b
+                else:
+                    assert (a < 8) == (b < 8)
+                seen.add((min(a, b), max(a, b)))
+        want = 64 if kind == 0 else 2 * 28
+        assert len(seen) == want
+    g = [[16 * me + p for p in range(16)] for me in range(2)]   # global block at each position
+    met = {}
+
+    def meet(u, v):
+        key = (min(u, v), max(u, v))
+        assert u != v and key not in met
+        met[key] = 1
+
+    for me in range(2):   # pairs inside each block
+        for p in range(16):
+            for t in range(7):
+                for q in range(4):
+                    a, b = order(1, 1, t, q)
+                    meet(8 * g[me][p] + a, 8 * g[me][p] + b)
+    for ph in range(3):
+        if ph == 1:
+            for k in range(8):
+                g[0][8 + k], g[1][k] = g[1][k], g[0][8 + k]
+        if ph == 2:
+            for k in range(8):
+                g[0][8 + k], g[1][8 + k] = g[1][8 + k], g[0][8 + k]
+        for r in range(15 if ph == 0 else 8):
+            held = [blk for w in range(8) for blk in order(0, ph, r, w)]
+            assert sorted(held) == list(range(16))
+            for me in range(2):
+                for w in range(8):
+                    a, b = order(0, ph, r, w)
+                    for t in range(8):
+                        for p in range(8):
+                            i, j = order(1, 0, t, p)
+                            meet(8 * g[me][a] + i, 8 * g[me][b] + (j - 8))
+    assert len(met) == 256 * 255 // 2
+    for args in [(2, 0, 0, 0), (0, 3, 0, 0), (0, 0, 15, 0), (0, 1, 8, 0), (0, 0, 0, 8), (1, 1, 7, 0),
+                 (1, 0, 8, 0), (1, 2, 0, 0)]:
+        with pytest.raises(hsvd.HsvdError):
+            order(*args)
+
+
 def test_jacobi_pair_rejects_bad_arguments(lib):
     for args in [(3, 0, 0), (4, 3, 0), (4, 0, 2), (0, 0, 0)]:
         with pytest.raises(hsvd.HsvdError):
