@@ -287,10 +287,9 @@ hsvd_status hsvd_step_times(hsvd_plan_t plan, double* ms, int32_t n, int32_t* ru
  *           for a plan.
  * Asynchronous on `stream`.  Sizes beyond the limits return
  * HSVD_EUNSUPPORTED; bad pointers or shapes HSVD_EINVAL.  The first call on
- * a device resolves the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call shares the
- * one array: calls that overlap on the GPU (two streams, two host threads)
- * race and corrupt each other; serialise them.  The sketch matrix is the one
+ * a device resolves the array's device address (cudaGetSymbolAddress).
+ * Every call shares the one array: calls that overlap on the GPU (two
+ * streams, two host threads) race and corrupt each other; serialise them.  The sketch matrix is the one
  * a plan with the default seed uses, so U and S agree with hsvd_run on a
  * 1 x 1 grid (block = whole matrix, FIXED_K k, PREC_F32, same power_iters)
  * within the FP32 tolerance. */

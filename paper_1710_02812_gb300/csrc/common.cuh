@@ -6,6 +6,7 @@
 // launch covers a whole level of Alg. 1 for every matrix of the batch.
 #pragma once
 
+#include <algorithm>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -253,6 +254,9 @@ struct TcTask {
   int kchunk_tiles;    // split-K: 64-wide K tiles per chunk (0: one chunk)
   int ldp;             // row stride of a partial tile (elements)
   float* part;         // split-K partials [chunk][M][ldp], or nullptr (write D)
+  // three-plane launches (FP32-grade products): planes 1 and 2 of A and B
+  // start a_pstride / b_pstride rows after plane 0 in the same tensor map
+  int a_pstride, b_pstride;
 };
 struct TcItem {
   int task, mt, kc;  // task, 128-row tile, K chunk
@@ -285,6 +289,29 @@ cudaError_t launch_convert_input(const void* X, bool x_is_bf16, int64_t ld, int6
                                  int64_t ldx, __nv_bfloat16* Xt, int64_t ldxt, cudaStream_t s);
 cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int bmax, int* err,
                            cudaStream_t s, int stages_override = 0);
+// The FP32-grade form: A and B given as three BF16 planes each (split3),
+// D = the six products hh + hm + mh + hl + lh + mm, the hh term in its own
+// tensor-memory accumulator (added in FP32 by the epilogue).  N = 128.
+cudaError_t launch_tc_gemm3(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int* err,
+                            cudaStream_t s);
+
+// FP32 -> three BF16 planes (split.cu): source rows x cols (ld lds); natural
+// planes (element (r, c) at dn[p psn + r ldn + c], zero up to orn x ocn) and/or
+// transposed planes (element (r, c) at dt[p pst + c ldt + r], zero up to
+// ort x oct); a null destination is skipped.
+struct Split3Task {
+  const float* src;
+  int64_t lds;
+  int rows, cols;
+  __nv_bfloat16* dn;
+  int64_t ldn, psn;
+  int orn, ocn;
+  __nv_bfloat16* dt;
+  int64_t ldt, pst;
+  int ort, oct;
+};
+void split3_items(const Split3Task& t, int task, std::vector<int3>& items);
+cudaError_t launch_split3(const Split3Task* tasks, const int3* items, int nitems, cudaStream_t s);
 std::vector<int> tc_stage_variants(int bmax);
 
 // Host-side helpers exported for checks without a GPU.

@@ -706,6 +706,7 @@ struct Builder {
         k.ldp = 0;
         k.part = nullptr;
       }
+      k.a_pstride = k.b_pstride = 0;
       tc.push_back(k);
       for (int mt = 0; mt < (M + 127) / 128; ++mt)
         for (int kc = 0; kc < nkc; ++kc) tci.push_back(TcItem{(int)t, mt, kc});
@@ -846,8 +847,212 @@ struct Builder {
     return o;
   }
 
+  // FP32-grade tensor-core CholeskyQR products (BF16-mixed path): the Gram
+  // G = A^T A and the product A R^-1 from three BF16 planes per operand
+  // (split3: natural planes of A for the product, transposed ones for the
+  // Gram, transposed planes of R^-1), six plane products accumulated on the
+  // tensor cores.  Used when every factor of the call has the static width
+  // kl (128 or 256) and at most 1024 rows; HSVD_NO_TC3 keeps the SIMT
+  // products.
+  static bool tc3_disabled() {
+    static const bool off = std::getenv("HSVD_NO_TC3") != nullptr;
+    return off;
+  }
+  bool tc3_eligible(const std::vector<OrthW>& ws, int kcapl) const {
+    if (!std::is_same<T, float>::value || !P.use_tc || tc3_disabled()) return false;
+    if (kcapl != 128 && kcapl != 256) return false;
+    for (const auto& w : ws)
+      if (w.k.dyn || w.k.cap != kcapl || w.kl != kcapl || w.h < 1 || w.h > 1024) return false;
+    return true;
+  }
+  struct Tc3Arena {
+    __nv_bfloat16 *yn = nullptr, *yt = nullptr, *rt = nullptr;
+    int mapn = -1, mapt = -1, mapr = -1;
+    int nw = 0, hpad = 0, kl = 0;
+  };
+  std::vector<Tc3Arena> tc3_arenas;
+  // plane arenas shared by every call of the same shape (the steps run in order)
+  Tc3Arena tc3_arena(int nw, int hpad, int kl) {
+    for (const auto& a : tc3_arenas)
+      if (a.nw == nw && a.hpad == hpad && a.kl == kl) return a;
+    Tc3Arena a;
+    a.nw = nw;
+    a.hpad = hpad;
+    a.kl = kl;
+    a.yn = alloc<__nv_bfloat16>((size_t)nw * 3 * hpad * kl);
+    a.yt = alloc<__nv_bfloat16>((size_t)nw * 3 * kl * hpad);
+    a.rt = alloc<__nv_bfloat16>((size_t)nw * 3 * kl * kl);
+    a.mapn = add_map(a.yn, (int64_t)nw * 3 * hpad, kl, kl, 128);
+    a.mapt = add_map(a.yt, (int64_t)nw * 3 * kl, hpad, hpad, 128);
+    a.mapr = add_map(a.rt, (int64_t)nw * 3 * kl, kl, kl, 128);
+    tc3_arenas.push_back(a);
+    return a;
+  }
+  void emit_tc3(const std::string& name, const std::vector<TcTask>& tc, const std::vector<TcItem>& items, double fl,
+                double by, int ntasks, int dim) {
+    PlanImpl* p = &P;
+    const size_t b1 = P.add_blob(tc), b2 = P.add_blob(items);
+    const int n2 = (int)items.size();
+    P.steps.push_back(Step{name, [p, b1, b2, n2](cudaStream_t s) {
+                             return launch_tc_gemm3(p->d_tmaps, p->table<TcTask>(b1), p->table<TcItem>(b2), n2,
+                                                    &p->d_status->tc_timeouts, s);
+                           }});
+    tag(8, ntasks, dim, fl, by);
+  }
+  void emit_split3(const std::string& name, const std::vector<Split3Task>& tasks, double by, int dim) {
+    if (tasks.empty()) return;
+    std::vector<int3> items;
+    for (size_t t = 0; t < tasks.size(); ++t) split3_items(tasks[t], (int)t, items);
+    PlanImpl* p = &P;
+    const size_t b1 = P.add_blob(tasks), b2 = P.add_blob(items);
+    const int n2 = (int)items.size();
+    P.steps.push_back(Step{name, [p, b1, b2, n2](cudaStream_t s) {
+                             return launch_split3(p->table<Split3Task>(b1), p->table<int3>(b2), n2, s);
+                           }});
+    tag(9, (int)tasks.size(), dim, 0, by);
+  }
+  void emit_orth_tc3(const std::string& name, const std::vector<OrthW>& ws, int passes, int kl) {
+    const int nw = (int)ws.size();
+    int hmax = 1;
+    for (const auto& w : ws) hmax = std::max(hmax, w.h);
+    const int hpad = ((hmax + 63) / 64) * 64;
+    const Tc3Arena ar = tc3_arena(nw, hpad, kl);
+    const int nt = kl / 128;
+    for (int pass = 0; pass < passes; ++pass) {
+      const bool last = pass == passes - 1;
+      std::vector<Split3Task> sp, sr;
+      std::vector<TcTask> gt, mt;
+      std::vector<TcItem> gi, mi;
+      std::vector<CholTask<T>> ch;
+      std::vector<GS> prod;
+      double gfl = 0, gby = 0, mfl = 0, mby = 0, sby = 0;
+      for (int t = 0; t < nw; ++t) {
+        const OrthW& w = ws[t];
+        const float* in = reinterpret_cast<const float*>(pass == 0 ? w.A : w.tmp);
+        const int64_t ldin = pass == 0 ? w.lda : w.kl;
+        Split3Task a;
+        std::memset(&a, 0, sizeof(a));
+        a.src = in;
+        a.lds = ldin;
+        a.rows = w.h;
+        a.cols = kl;
+        a.dn = ar.yn + (size_t)t * 3 * hpad * kl;
+        a.ldn = kl;
+        a.psn = (int64_t)hpad * kl;
+        a.orn = hpad;
+        a.ocn = kl;
+        a.dt = ar.yt + (size_t)t * 3 * kl * hpad;
+        a.ldt = hpad;
+        a.pst = (int64_t)kl * hpad;
+        a.ort = kl;
+        a.oct = hpad;
+        sp.push_back(a);
+        sby += (double)w.h * kl * 4 + 2.0 * 3 * hpad * kl * 2;
+        // Gram: the upper 128 x 128 tiles (m-tile <= n-tile)
+        for (int n = 0; n < nt; ++n) {
+          TcTask k;
+          std::memset(&k, 0, sizeof(k));
+          k.amap = ar.mapt;
+          k.a_row0 = t * 3 * kl;
+          k.a_col0 = 0;
+          k.a_pstride = kl;
+          k.bmap = ar.mapt;
+          k.b_row0 = t * 3 * kl + n * 128;
+          k.b_pstride = kl;
+          k.b2_row0 = -1;
+          k.M = (n + 1) * 128;
+          k.N = 128;
+          k.K = hpad;
+          k.D = reinterpret_cast<float*>(w.G) + n * 128;
+          k.ldd = w.kl;
+          for (int m = 0; m <= n; ++m) gi.push_back(TcItem{(int)gt.size(), m, 0});
+          gt.push_back(k);
+          gfl += 2.0 * (n + 1) * 128 * 128 * w.h;
+        }
+        gby += 3.0 * kl * hpad * 2 + (double)kl * kl * 2;
+        CholTask<T> c;
+        std::memset(&c, 0, sizeof(c));
+        c.G = w.G;
+        c.ldg = w.kl;
+        c.k = w.k;
+        c.Rinv = w.Rinv;
+        c.ldri = w.kl;
+        if (w.R) {
+          if (passes == 1) {
+            c.R = w.R;
+          } else if (pass == 0) {
+            c.R = w.R1;
+          } else if (w.R2) {
+            // R = R2 R1 as its own product (as the SIMT path does for wide factors)
+            c.R = w.R2;
+            GS g = nn(w.R2, w.kl, w.kl, w.k, w.R1, w.kl, w.k, w.R, w.kl);
+            g.M = w.k;
+            prod.push_back(g);
+          } else {
+            c.R = w.R;
+            c.Rprev = w.R1;
+            c.ldrp = w.kl;
+          }
+          c.ldr = w.kl;
+        }
+        ch.push_back(c);
+        T* out = last ? w.Q : w.tmp;
+        if (out) {
+          Split3Task r;
+          std::memset(&r, 0, sizeof(r));
+          r.src = reinterpret_cast<const float*>(w.Rinv);
+          r.lds = w.kl;
+          r.rows = kl;
+          r.cols = kl;
+          r.dt = ar.rt + (size_t)t * 3 * kl * kl;
+          r.ldt = kl;
+          r.pst = (int64_t)kl * kl;
+          r.ort = kl;
+          r.oct = kl;
+          sr.push_back(r);
+          // A R^-1 with R^-1 upper triangular: output column tile n needs
+          // K = (n + 1) 128
+          for (int n = 0; n < nt; ++n) {
+            TcTask k;
+            std::memset(&k, 0, sizeof(k));
+            k.amap = ar.mapn;
+            k.a_row0 = t * 3 * hpad;
+            k.a_col0 = 0;
+            k.a_pstride = hpad;
+            k.bmap = ar.mapr;
+            k.b_row0 = t * 3 * kl + n * 128;
+            k.b_pstride = kl;
+            k.b2_row0 = -1;
+            k.M = w.h;
+            k.N = 128;
+            k.K = (n + 1) * 128;
+            k.D = reinterpret_cast<float*>(out) + n * 128;
+            k.ldd = w.kl;
+            for (int m = 0; m < (w.h + 127) / 128; ++m) mi.push_back(TcItem{(int)mt.size(), m, 0});
+            mt.push_back(k);
+            mfl += 2.0 * w.h * 128 * (n + 1) * 128;
+          }
+          mby += 3.0 * hpad * kl * 2 + 3.0 * kl * kl * 2 + (double)w.h * kl * 4;
+        }
+      }
+      const std::string tag3 = name + ".p" + std::to_string(pass + 1);
+      emit_split3(tag3 + ".split", sp, sby, kl);
+      emit_tc3(tag3 + ".gram", gt, gi, gfl, gby, nw, kl);
+      emit_chol(tag3 + ".chol", ch, kl);
+      emit_gemm(tag3 + ".R", prod, false);
+      if (!mt.empty()) {
+        emit_split3(tag3 + ".rsplit", sr, (double)sr.size() * kl * kl * (4 + 6), kl);
+        emit_tc3(tag3 + ".mul", mt, mi, mfl, mby, nw, kl);
+      }
+    }
+  }
+
   void emit_orth(const std::string& name, const std::vector<OrthW>& ws, int passes, int kcapl) {
     if (ws.empty()) return;
+    if (tc3_eligible(ws, kcapl)) {
+      emit_orth_tc3(name, ws, passes, kcapl);
+      return;
+    }
     // For 128-wide FP32 factors the product R = R2 R1 runs as its own GEMM:
     // staging both triangles in the Cholesky kernel takes 132 KB of shared
     // memory, one CTA per SM, and doubles the factorisation's time.

@@ -347,6 +347,209 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const CUtensorMap* __restric
   if (warp == 0) tmem_dealloc(tacc, ncols);
 }
 
+// A diagonal tile of a Gram reads the same 128 rows as A and as B: they are
+// loaded once.
+__device__ __forceinline__ bool tc3_same_operand(const TcTask& tk, const TcItem& it) {
+  return tk.bmap == tk.amap && tk.b_row0 == tk.a_row0 + it.mt * TC_BM && tk.b_pstride == tk.a_pstride &&
+         tk.a_col0 == 0;
+}
+
+// FP32-grade products from three BF16 planes per operand (split3): per K
+// tile the producer loads A0, A1, A2 (128 x 64 each) and B0, B1, B2 (128 x 64
+// each), the issuer accumulates A0 B0 into the main accumulator and
+// A1 B1 + A2 B0 + A0 B2 + A1 B0 + A0 B1 into a second one.  The tensor cores'
+// FP32 accumulation loses about half an ulp toward zero per accumulation
+// step; with the small terms in their own accumulator, the long accumulation
+// at full magnitude is the main term's only (K / 16 steps).  The epilogue
+// adds the two in FP32.  Roles, barriers, the persistent item loop and the
+// bounded waits are those of k_tc_gemm; N = 128 and no split-K.
+__global__ void __launch_bounds__(192, 1) k_tc_gemm3(const CUtensorMap* __restrict__ maps,
+                                                     const TcTask* __restrict__ tasks,
+                                                     const TcItem* __restrict__ items, int nitems, int stages,
+                                                     int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[4];
+  __shared__ __align__(8) uint64_t empty_bar[4];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  constexpr int BN = 128;
+  constexpr uint32_t tile_bytes = TC_BM * TC_BK * 2;  // one 128 x 64 BF16 plane tile
+  constexpr uint32_t stage_bytes = 6 * tile_bytes;
+  constexpr uint32_t acc_cols = BN;
+  constexpr uint32_t ncols = 4 * acc_cols;  // two items x (main, small)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base_s = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* base = smem_raw + (base_s - smem_u32(smem_raw));
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 4);
+    }
+    mbar_init(&done_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base;
+  auto fail = [&]() {
+    if (atomicExch(&failed, 1) == 0) atomicAdd(err, 1);
+  };
+
+  if (warp == 0) {
+    // ---- producer
+    int g = 0;
+    if (lane == 0) {
+      for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x) {
+        const TcItem it = items[i];
+        const TcTask tk = tasks[it.task];
+        const int nk = (tk.K + TC_BK - 1) / TC_BK;
+        const CUtensorMap* amap = maps + tk.amap;
+        const CUtensorMap* bmap = maps + tk.bmap;
+        const int arow = tk.a_row0 + it.mt * TC_BM;
+        const bool same = tc3_same_operand(tk, it);
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % stages;
+          if (g >= stages && !mbar_wait(&empty_bar[s], ((g / stages) - 1) & 1)) {
+            fail();
+            break;
+          }
+          if (*(volatile int*)&failed) break;
+          unsigned char* st = base + s * stage_bytes;
+          mbar_arrive_expect_tx(&full_bar[s], same ? stage_bytes / 2 : stage_bytes);
+          const int kx = kt * TC_BK;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            tma_load_2d(st + p * tile_bytes, amap, &full_bar[s], tk.a_col0 + kx, arow + p * tk.a_pstride);
+            if (!same)
+              tma_load_2d(st + (3 + p) * tile_bytes, bmap, &full_bar[s], kx, tk.b_row0 + p * tk.b_pstride);
+          }
+        }
+      }
+      if (*(volatile int*)&failed) {
+        // copies still in flight land before the shared memory is released
+        for (int t = g > stages ? g - stages : 0; t < g; ++t) mbar_wait(&full_bar[t % stages], (t / stages) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: item j into the accumulator pair (j & 1)
+    if (lane == 0) {
+      int g = 0, j = 0;
+      const uint32_t idesc = idesc_bf16_f32(TC_BM, BN);
+      for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x, ++j) {
+        const TcItem it = items[i];
+        const TcTask tk = tasks[it.task];
+        const int nk = (tk.K + TC_BK - 1) / TC_BK;
+        const bool same = tc3_same_operand(tk, it);
+        const int a = j & 1;
+        if (j >= 2 && !mbar_wait(&tempty_bar[a], ((j >> 1) - 1) & 1)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dm = tacc + static_cast<uint32_t>(a) * 2 * acc_cols;  // main term
+        const uint32_t ds = dm + acc_cols;                                   // small terms
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % stages;
+          if (!mbar_wait(&full_bar[s], (g / stages) & 1)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = base_s + s * stage_bytes;
+          const uint32_t sb = same ? sa : sa + 3 * tile_bytes;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t a0 = desc_k_sw128(sa + off), a1 = desc_k_sw128(sa + tile_bytes + off),
+                           a2 = desc_k_sw128(sa + 2 * tile_bytes + off);
+            const uint64_t b0 = desc_k_sw128(sb + off), b1 = desc_k_sw128(sb + tile_bytes + off),
+                           b2 = desc_k_sw128(sb + 2 * tile_bytes + off);
+            const uint32_t acc = (kt | kk) != 0;
+            umma_bf16(dm, a0, b0, idesc, acc);
+            umma_bf16(ds, a1, b1, idesc, acc);
+            umma_bf16(ds, a2, b0, idesc, 1u);
+            umma_bf16(ds, a0, b2, idesc, 1u);
+            umma_bf16(ds, a1, b0, idesc, 1u);
+            umma_bf16(ds, a0, b1, idesc, 1u);
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull_bar[a]);
+      }
+      // every MMA of this CTA has completed once done_bar fires
+      umma_commit(&done_bar);
+      mbar_wait(&done_bar, 0);
+    }
+  } else {
+    // ---- epilogue (warps 2-5): TMEM lane quarter (warp % 4) -> rows
+    const int q = warp & 3;
+    const int row_in = q * 32 + lane;
+    int j = 0;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x, ++j) {
+      const int a = j & 1;
+      bool got = false;
+      {
+        const long long t0 = clock64();
+        const uint32_t par = (j >> 1) & 1;
+        while (!(got = mbar_test(&tfull_bar[a], par))) {
+          if (*(volatile int*)&failed || clock64() - t0 > TC_WAIT_CYCLES) break;
+        }
+      }
+      if (!got) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      const TcItem it = items[i];
+      const TcTask tk = tasks[it.task];
+      const int gm = it.mt * TC_BM + row_in;
+      const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+      const uint32_t srcm = tacc + static_cast<uint32_t>(a) * 2 * acc_cols + lane_off;
+      const uint32_t srcs = srcm + acc_cols;
+      float v[32], w[32];
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        tmem_ld32(srcm + static_cast<uint32_t>(c0), v);
+        tmem_ld32(srcs + static_cast<uint32_t>(c0), w);
+        if (gm < tk.M) {
+          float* drow = tk.D + static_cast<int64_t>(gm) * tk.ldd + c0;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] += w[e];
+          if (c0 + 32 <= tk.N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              *reinterpret_cast<float4*>(drow + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              if (c0 + e < tk.N) drow[e] = v[e];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[a])) : "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tacc, ncols);
+}
+
 // One CTA per (task, 16-row tile): rows x columns in float4 groups when the
 // strides allow, chunks summed in order.
 __global__ void __launch_bounds__(256) k_tc_reduce(const TcRedTask* __restrict__ tasks,
@@ -473,6 +676,29 @@ cudaError_t launch_tc_gemm(const void* maps, const TcTask* tasks, const TcItem* 
   const int grid = nitems < nsm ? nitems : nsm;
   k_tc_gemm<<<grid, 192, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, nitems, stages, bmax, err,
                                      first_wait);
+  return cudaGetLastError();
+}
+
+// Two stages of six 16 KB plane tiles (one CTA per SM: the tensor memory of
+// two items' pairs of accumulators is the SM's 512 columns).
+cudaError_t launch_tc_gemm3(const void* maps, const TcTask* tasks, const TcItem* items, int nitems, int* err,
+                            cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  const int stages = 2;
+  const size_t bytes = static_cast<size_t>(stages) * 6 * TC_BM * TC_BK * 2 + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  static const int nsm = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return v > 0 ? v : 152;
+  }();
+  const int grid = nitems < nsm ? nitems : nsm;
+  k_tc_gemm3<<<grid, 192, bytes, s>>>(static_cast<const CUtensorMap*>(maps), tasks, items, nitems, stages, err);
   return cudaGetLastError();
 }
 
