@@ -41,7 +41,9 @@ __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bf
 // bases allow, element by element otherwise).  The transposed planes go
 // through shared memory so that their stores also run along rows.
 __global__ void __launch_bounds__(256) k_split3(const Split3Task* __restrict__ tasks, const int3* __restrict__ items) {
-  __shared__ __nv_bfloat16 sh[3][SP_T][SP_T + 8];  // [plane][source column][source row]
+  // [plane][source column][source row]; rows of 65 elements put the 16
+  // column quads of a warp's stores in 16 different banks
+  __shared__ __nv_bfloat16 sh[3][SP_T][SP_T + 1];
   const int3 it = items[blockIdx.x];
   const Split3Task tk = tasks[it.x];
   const int r0 = it.y * SP_T, c0 = it.z * SP_T;
