@@ -636,8 +636,29 @@ struct Builder {
     }
     const int kpad = ((kmax + 63) / 64) * 64;
     const int per = lo ? 2 : 1;
-    __nv_bfloat16* arena = alloc<__nv_bfloat16>((size_t)ops.size() * per * bmax * kpad);
-    const int bmap = add_map(arena, (int64_t)ops.size() * per * bmax, kpad, kpad, bmax);
+    // one transposed copy per distinct factor: ops that share a factor (the
+    // sketch matrix of every block) read the same arena rows
+    std::vector<int> slot(ops.size());
+    std::vector<size_t> first;  // op converted into each slot
+    for (size_t t = 0; t < ops.size(); ++t) {
+      const InputOp& o = ops[t];
+      const int K = o.xt ? o.h : o.w;
+      int found = -1;
+      for (size_t q = 0; q < first.size() && found < 0; ++q) {
+        const InputOp& f = ops[first[q]];
+        if (f.B == o.B && f.ldb == o.ldb && (f.xt ? f.h : f.w) == K && f.N.cap == o.N.cap && f.N.dyn == o.N.dyn)
+          found = (int)q;
+        if (q > 0) break;  // factors are either all shared or all distinct: compare with the first only
+      }
+      if (found < 0) {
+        found = (int)first.size();
+        first.push_back(t);
+      }
+      slot[t] = found;
+    }
+    const size_t nslot = first.size();
+    __nv_bfloat16* arena = alloc<__nv_bfloat16>(nslot * per * bmax * kpad);
+    const int bmap = add_map(arena, (int64_t)nslot * per * bmax, kpad, kpad, bmax);
     std::vector<BtTask> bt;
     std::vector<int3> bti;
     std::vector<TcTask> tc;
@@ -645,21 +666,24 @@ struct Builder {
     std::vector<TcRedTask> red;
     std::vector<int2> rdi;
     double flops = 0, bytes = 0, rbytes = 0;
-    for (size_t t = 0; t < ops.size(); ++t) {
-      const InputOp& o = ops[t];
-      const int M = o.xt ? o.w : o.h, K = o.xt ? o.h : o.w;
+    for (size_t q = 0; q < nslot; ++q) {
+      const InputOp& o = ops[first[q]];
       BtTask b;
       b.B = reinterpret_cast<const float*>(o.B);
       b.ldb = o.ldb;
-      b.K = K;
+      b.K = o.xt ? o.h : o.w;
       b.N = o.N;
-      b.hi = arena + (size_t)t * per * bmax * kpad;
+      b.hi = arena + q * per * bmax * kpad;
       b.lo = lo ? b.hi + (size_t)bmax * kpad : nullptr;
       b.kpad = kpad;
       b.bmax = bmax;
       bt.push_back(b);
       for (int nt = 0; nt < bmax / 32 + (bmax % 32 ? 1 : 0); ++nt)
-        for (int kt = 0; kt < kpad / 32; ++kt) bti.push_back(make_int3((int)t, nt, kt));
+        for (int kt = 0; kt < kpad / 32; ++kt) bti.push_back(make_int3((int)q, nt, kt));
+    }
+    for (size_t t = 0; t < ops.size(); ++t) {
+      const InputOp& o = ops[t];
+      const int M = o.xt ? o.w : o.h, K = o.xt ? o.h : o.w;
       // the view matrix is X (or X^T when the tree is transposed)
       const bool use_xt = o.xt != o.vt;  // read the stored X^T copy
       TcTask k;
@@ -667,7 +691,7 @@ struct Builder {
       k.a_row0 = (int)(o.xt ? o.c0 : o.r0);
       k.a_col0 = (int)(o.xt ? o.r0 : o.c0);
       k.bmap = bmap;
-      k.b_row0 = (int)(t * per * bmax);
+      k.b_row0 = (int)((size_t)slot[t] * per * bmax);
       k.b2_row0 = lo ? k.b_row0 + bmax : -1;
       k.M = M;
       k.N = o.N.cap;
@@ -719,7 +743,7 @@ struct Builder {
     P.steps.push_back(Step{name + ".bt", [p, b1, b2, n2](cudaStream_t s) {
                              return launch_make_bt(p->table<BtTask>(b1), p->table<int3>(b2), n2, s);
                            }});
-    tag(9, (int)ops.size(), bmax, 0, (double)ops.size() * bmax * kpad * 2 * per);
+    tag(9, (int)nslot, bmax, 0, (double)nslot * bmax * kpad * 2 * per);
     {
       const std::vector<int> depths = tc_stage_variants(bmax);
       auto choice = std::make_shared<int>(0);
@@ -2391,7 +2415,11 @@ hsvd_status hsvd_run_host(hsvd_plan_t plan, const void* const* A, const int64_t*
     // the device can address the host buffer (page-locked memory, reached over
     // NVLink-C2C on Grace systems) that step reads it in place, and the
     // transfer overlaps the conversion instead of preceding it.
-    if (P.mixed) {
+    static const bool inplace = [] {
+      const char* e = std::getenv("HSVD_HOST_INPLACE");
+      return !(e && e[0] == '0');
+    }();
+    if (P.mixed && inplace) {
       cudaPointerAttributes attr;
       if (cudaPointerGetAttributes(&attr, A[b]) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
           attr.devicePointer) {

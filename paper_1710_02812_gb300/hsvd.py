@@ -468,19 +468,20 @@ class Plan:
         hsvd_run_host(self._h, ptrs, lda, stream)
 
     def factors(self, idx=0, stream=None):
-        """Copy (U, S, V) of matrix idx to host numpy arrays (column-major
-        in the library, returned as ordinary m x r / n x r arrays)."""
+        """Copy (U, S, V) of matrix idx to host numpy arrays: U is m x r and V
+        n x r, returned as views with column-major strides (the library's
+        layout; no host-side transposing copy), S has r entries."""
         dt = self.factor_dtype
         m, n, kc = self.m[idx], self.n[idx], self.kcap
-        U = np.zeros((kc, m), dtype=dt)  # column-major m x kc == row-major kc x m
-        V = np.zeros((kc, n), dtype=dt)
-        S = np.zeros(kc, dtype=dt)
+        U = np.empty((kc, m), dtype=dt)  # column-major m x kc == row-major kc x m
+        V = np.empty((kc, n), dtype=dt)
+        S = np.empty(kc, dtype=dt)
         r = ctypes.c_int32()
         code = hsvd_factors(self._h, idx, ctypes.byref(r), U.ctypes.data, m, S.ctypes.data, V.ctypes.data, n,
                             WHERE["host"], _stream_ptr(stream))
         _check(code, "hsvd_factors")
         k = r.value
-        return U[:k].T.copy(), S[:k].copy(), V[:k].T.copy()
+        return U[:k].T, S[:k], V[:k].T
 
     def factors_device(self, U, S, V, idx=0, stream=None) -> int:
         """Write column-major factors into device tensors U (kcap x m storage),
