@@ -96,6 +96,7 @@ struct PlanImpl {
   size_t in_elem = 4;  // input element size as given to hsvd_run
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  size_t arena_persist = 0;  // the persistent part; stage scratch follows it
   char* tables = nullptr;
   size_t tables_bytes = 0;
   MatRef* d_mats = nullptr;
@@ -260,16 +261,52 @@ struct Builder {
   using GS = GemmTask<T, T, T>;
   PlanImpl& P;
   char* base;
-  size_t off = 0;
+  size_t off = 0;  // persistent part of the arena
+  // Scratch: the temporaries of one stage (the block stage, one level of a
+  // MAT tree, the slab step) live in a region after the persistent part that
+  // the next stage reuses; the steps run in stream order, so a stage's writes
+  // follow every read of the previous one.  Stage outputs (factors) and what
+  // is read after a run stay persistent.
+  bool scratch = false;
+  size_t soff = 0, smax = 0;
+  size_t sbase;  // offset of the scratch region (the persistent size, from the sizing pass)
 
-  Builder(PlanImpl& p, char* b) : P(p), base(b) {}
+  Builder(PlanImpl& p, char* b, size_t scratch_base) : P(p), base(b), sbase(scratch_base) {}
 
   template <class X>
   X* alloc(size_t count) {
     const size_t bytes = std::max<size_t>(count * sizeof(X), 16);
+    if (scratch) {
+      const size_t o = soff;
+      soff = (soff + bytes + 255) & ~size_t(255);
+      smax = std::max(smax, soff);
+      return reinterpret_cast<X*>(reinterpret_cast<uintptr_t>(base) + sbase + o);
+    }
     const size_t o = off;
     off = (off + bytes + 255) & ~size_t(255);
     return reinterpret_cast<X*>(reinterpret_cast<uintptr_t>(base) + o);
+  }
+  // persistent whatever the mode
+  template <class X>
+  X* palloc(size_t count) {
+    const bool s = scratch;
+    scratch = false;
+    X* p = alloc<X>(count);
+    scratch = s;
+    return p;
+  }
+  static bool scratch_disabled() {  // HSVD_NO_SCRATCH: every buffer persistent (for comparison)
+    static const bool off = std::getenv("HSVD_NO_SCRATCH") != nullptr;
+    return off;
+  }
+  void scratch_begin() {
+    scratch = true;
+    soff = 0;
+    tc3_reset();
+  }
+  void scratch_end() {
+    scratch = false;
+    tc3_reset();
   }
 
   struct Factor {
@@ -281,10 +318,10 @@ struct Builder {
 
   Factor new_factor(int h) {
     Factor f;
-    f.U = alloc<T>((size_t)h * P.kcap);
+    f.U = palloc<T>((size_t)h * P.kcap);
     f.h = h;
-    f.sig = alloc<T>(P.kcap);
-    f.rank = alloc<int>(1);
+    f.sig = palloc<T>(P.kcap);
+    f.rank = palloc<int>(1);
     return f;
   }
 
@@ -895,6 +932,7 @@ struct Builder {
     int nw = 0, hpad = 0, kl = 0;
   };
   std::vector<Tc3Arena> tc3_arenas;
+  void tc3_reset() { tc3_arenas.clear(); }
   // plane arenas shared by every call of the same shape (the steps run in order)
   Tc3Arena tc3_arena(int nw, int hpad, int kl) {
     for (const auto& a : tc3_arenas)
@@ -1232,7 +1270,7 @@ struct Builder {
 
   // Binary MAT tree over each list (Alg. 1, DoMergeOfSlices), all lists and
   // all pairs of one level in one batch.
-  std::vector<Factor> tree(const std::string& name, std::vector<std::vector<Factor>> lists) {
+  std::vector<Factor> tree(const std::string& name, std::vector<std::vector<Factor>> lists, bool use_scratch = false) {
     int level = 0;
     for (;;) {
       std::vector<std::pair<Factor, Factor>> pairs;
@@ -1251,9 +1289,11 @@ struct Builder {
       }
       if (!any) break;
       std::vector<Factor> outs;
+      if (use_scratch) scratch_begin();  // each level's temporaries reuse the region
       auto ms = make_merges(pairs, outs);
       for (size_t i = 0; i < where.size(); ++i) next[where[i].first][where[i].second] = outs[i];
       emit_merge_level(name + ".L" + std::to_string(level), ms);
+      if (use_scratch) scratch_end();
       lists.swap(next);
       ++level;
     }
@@ -1479,6 +1519,8 @@ struct Builder {
     }
 
     // ---------------------------------------------------- level 0: blocks
+    const bool use_scratch = !scratch_disabled();
+    if (use_scratch) scratch_begin();
     std::vector<BlockW> bw;
     std::vector<std::vector<std::vector<Factor>>> slab_leaves(P.batch);
     for (int b = 0; b < P.batch; ++b) {
@@ -1591,6 +1633,7 @@ struct Builder {
       emit_jacobi("block.core", jt, kp, kp, false, tp);
       emit_gemm("block.U", ut, false);
     }
+    if (use_scratch) scratch_end();
 
     // ---------------------------------------------------- column MAT trees
     std::vector<std::vector<Factor>> lists;
@@ -1600,12 +1643,13 @@ struct Builder {
         lists.push_back(slab_leaves[b][j]);
         owner.push_back({b, (int)j});
       }
-    std::vector<Factor> slabU = tree("colmerge", lists);
+    std::vector<Factor> slabU = tree("colmerge", lists, use_scratch);
 
     // ---------------------------------------------------- slab step
     // V_j, Sigma_j = SVD(U_j^T X_j): Z_j^T = X_j^T U_j = Q_z R_z,
     // R_z = A S C^T  =>  V_j = Q_z A.
     std::vector<std::vector<Factor>> row_lists(P.batch);
+    if (use_scratch) scratch_begin();
     {
       std::vector<InputOp> ops;
       std::vector<OrthW> ow;
@@ -1647,9 +1691,10 @@ struct Builder {
       emit_jacobi("slab.core", jt, kc, kc, false, tp);
       emit_gemm("slab.V", vt_gemm, false);
     }
+    if (use_scratch) scratch_end();
 
     // ---------------------------------------------------- row MAT trees
-    std::vector<Factor> vhat = tree("rowmerge", row_lists);
+    std::vector<Factor> vhat = tree("rowmerge", row_lists, use_scratch);
     for (int b = 0; b < P.batch; ++b)
       P.roots.push_back(PlanImpl::Root{vhat[b].U, vhat[b].sig, vhat[b].rank, (int)(vt ? P.m[b] : P.n[b])});
     if (P.stop_rows) {
@@ -1847,9 +1892,12 @@ struct Builder {
 template <class T, class TA>
 hsvd_status build_plan(PlanImpl& P) {
   {
-    Builder<T, TA> sizing(P, nullptr);
+    // the sizing pass places scratch far from the persistent offsets, so no
+    // two buffers of it compare equal where the real pass's would differ
+    Builder<T, TA> sizing(P, nullptr, size_t(1) << 60);
     sizing.build();
-    P.arena_bytes = sizing.off;
+    P.arena_persist = sizing.off;
+    P.arena_bytes = sizing.off + sizing.smax;
   }
   P.steps.clear();
   P.init_steps.clear();
@@ -1864,9 +1912,9 @@ hsvd_status build_plan(PlanImpl& P) {
     cudaGetLastError();
     return HSVD_ENOMEM;
   }
-  Builder<T, TA> real(P, P.arena);
+  Builder<T, TA> real(P, P.arena, P.arena_persist);
   real.build();
-  if (real.off != P.arena_bytes) return HSVD_ECUDA;  // layout must be identical
+  if (real.off + real.smax != P.arena_bytes) return HSVD_ECUDA;  // layout must be identical
   if (real.map_failed) return HSVD_EUNSUPPORTED;
   if (!P.tmaps.empty()) {
     if (cudaMalloc(&P.d_tmaps, P.tmaps.size() * 128) != cudaSuccess) {
