@@ -35,15 +35,20 @@ __device__ __forceinline__ void cs_dims(const JacobiTask<float>& tk, int& nr, in
   }
 }
 
+// et: a merge core is loaded transposed (slot j holds row j of E).
 template <int NT, int LDM>
-__device__ __forceinline__ void cs_load_core(const JacobiTask<float>& tk, float* Mw, int me, int nr, int nc, int k1) {
+__device__ __forceinline__ void cs_load_core(const JacobiTask<float>& tk, float* Mw, int me, int nr, int nc, int k1,
+                                             bool et = false) {
   const int col0 = me * CS_COLS;
   // a core read from a column-major source runs down its columns; the merge
   // core's factors and row-major sources run along rows (coalesced reads)
-  const bool down = tk.load == 0 && tk.rs == 1;
+  // (a transposed merge core runs down its slots: along the rows of E)
+  const bool tr = et && tk.load == 1;
+  const bool down = (tk.load == 0 && tk.rs == 1) || tr;
 #pragma unroll 4
   for (int e = threadIdx.x; e < CS_NROWS * CS_COLS; e += NT) {
-    const int i = down ? e % CS_NROWS : e / CS_COLS, j = down ? e / CS_NROWS : e % CS_COLS, gj = col0 + j;
+    const int i0 = down ? e % CS_NROWS : e / CS_COLS, j = down ? e / CS_NROWS : e % CS_COLS, s = col0 + j;
+    const int i = tr ? s : i0, gj = tr ? i0 : s;  // element (i, gj) of the core goes to slot s, row i0
     float v = 0.f;
     if (gj < nc && i < nr) {
       if (tk.load == 0) {
@@ -60,7 +65,7 @@ __device__ __forceinline__ void cs_load_core(const JacobiTask<float>& tk, float*
         v = tk.R[(int64_t)(i - k1) * tk.ldr + (gj - k1)] * tk.s2[gj - k1];
       }
     }
-    Mw[j * LDM + i] = v;
+    Mw[j * LDM + i0] = v;
   }
 }
 

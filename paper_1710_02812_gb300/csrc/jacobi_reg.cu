@@ -242,6 +242,127 @@ __device__ __forceinline__ bool rr_angle(float a, float b, float c, float ab, fl
   return rot;
 }
 
+// ---- Householder QR of E^T before the sweeps (merge cores).  For the merge
+// core E = [[S1, P S2], [0, R S2]] (upper triangular, columns of very
+// different scales) the cyclic sweeps converge slowly; on R_e^T, where
+// E^T = Q_e R_e, they converge as fast as on the block cores (E = R_e^T Q_e^T
+// has the left singular vectors of R_e^T).  The CTAs hold the columns of E^T
+// (rows of E); panels of 8 columns are factored by the warp holding them
+// (Householder: beta = -sign(alpha) |x|, v = x / (alpha - beta) below the
+// diagonal and 1 on it, tau = (beta - alpha) / beta; tau = 0 when the column
+// is already zero below the diagonal) and their reflectors applied in order
+// to every later column of both CTAs.
+
+// rows held by lane ln: element q (0..7) of a column is row rr_row(q, ln)
+__device__ __forceinline__ int rr_row(int q, int ln) { return (q < 4 ? 0 : 128) + 4 * ln + (q & 3); }
+
+__device__ __forceinline__ void rr_unpack8(const uint64_t (&c)[4], float (&v)[8]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) f2_unpack(c[u], v[2 * u], v[2 * u + 1]);
+}
+__device__ __forceinline__ void rr_pack8(const float (&v)[8], uint64_t (&c)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) c[u] = f2_pack(v[2 * u], v[2 * u + 1]);
+}
+__device__ __forceinline__ float rr_warp_sum(float s) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(RR_FULL, s, off);
+  return s;
+}
+
+// Factor panel P (8 columns: register block BASE of this warp): the
+// reflectors' vectors into vs[8][256] (zero above the diagonal), tau into
+// taus[8]; the columns become the panel of R (zero below the diagonal).
+template <int BASE>
+__device__ __forceinline__ void rr_panel(uint64_t (&x)[16][4], int P, float* vs, float* taus, int ln) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = 8 * P + c;
+    float xv[8];
+    rr_unpack8(x[BASE + c], xv);
+    float s = 0.f, al = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = rr_row(q, ln);
+      s += r > j ? xv[q] * xv[q] : 0.f;
+      al += r == j ? xv[q] : 0.f;  // one lane holds row j
+    }
+    s = rr_warp_sum(s);
+    al = rr_warp_sum(al);
+    const bool refl = s > 0.f;
+    const float be = refl ? -copysignf(sqrtf(fmaf(al, al, s)), al) : al;
+    const float tau = refl ? (be - al) / be : 0.f;
+    const float sc = refl ? 1.f / (al - be) : 0.f;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = rr_row(q, ln);
+      v[q] = r > j ? xv[q] * sc : (r == j ? 1.f : 0.f);
+      xv[q] = r > j ? 0.f : (r == j ? be : xv[q]);
+    }
+    rr_pack8(xv, x[BASE + c]);
+    // apply to the panel's later columns: x -= tau (v . x) v
+    float d[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      float part = 0.f;
+      if (e > c) {
+        float y[8];
+        rr_unpack8(x[BASE + e], y);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part = fmaf(v[q], y[q], part);
+      }
+      d[e] = part;
+    }
+    const float dr = rr_reduce8(d, ln);  // lane group p: the sum for column p
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (e > c) {
+        const float de = -tau * __shfl_sync(RR_FULL, dr, 4 * e);
+        float y[8];
+        rr_unpack8(x[BASE + e], y);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = fmaf(de, v[q], y[q]);
+        rr_pack8(y, x[BASE + e]);
+      }
+    }
+    float4* vo = reinterpret_cast<float4*>(vs + c * 256);
+    vo[ln] = make_float4(v[0], v[1], v[2], v[3]);
+    vo[32 + ln] = make_float4(v[4], v[5], v[6], v[7]);
+    if (ln == 0) taus[c] = tau;
+  }
+}
+
+// Apply the 8 reflectors of a panel (vs, taus) in order to register block BASE.
+template <int BASE>
+__device__ __forceinline__ void rr_apply_panel(uint64_t (&x)[16][4], const float* vs, const float* taus, int ln) {
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    const float4* vi = reinterpret_cast<const float4*>(vs + i * 256);
+    const float4 a = vi[ln], b = vi[32 + ln];
+    const uint64_t v2[4] = {f2_pack(a.x, a.y), f2_pack(a.z, a.w), f2_pack(b.x, b.y), f2_pack(b.z, b.w)};
+    const float tau = taus[i];
+    float d[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      uint64_t acc = f2_mul(v2[0], x[BASE + c][0]);
+#pragma unroll
+      for (int u = 1; u < 4; ++u) acc = f2_fma(v2[u], x[BASE + c][u], acc);
+      float lo, hi;
+      f2_unpack(acc, lo, hi);
+      d[c] = lo + hi;
+    }
+    const float dr = rr_reduce8(d, ln);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float de = -tau * __shfl_sync(RR_FULL, dr, 4 * c);
+      const uint64_t de2 = f2_pack(de, de);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[BASE + c][u] = f2_fma(de2, v2[u], x[BASE + c][u]);
+    }
+  }
+}
+
 // One step: the 8 pairs (rr_cx, rr_cy) of kind K, step T.  bc: this step's
 // half of the warp's angle table (8 entries of (-alpha, -alpha, beta, beta)).
 template <int K, int T>
@@ -343,8 +464,9 @@ __device__ __forceinline__ void rr_transition(uint64_t (&x)[16][4], float2* nd, 
   __syncwarp();
 }
 
+// pre_qr: merge cores take the QR of E^T before the sweeps.
 __global__ void __launch_bounds__(RR_THREADS, 1) k_jacobi_rr(const JacobiTask<float>* __restrict__ tasks,
-                                                            TruncParams tp, DevStatus* __restrict__ st) {
+                                                            TruncParams tp, DevStatus* __restrict__ st, int pre_qr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* __restrict__ Mw = reinterpret_cast<float*>(smem_raw);
   float* __restrict__ Stage = Mw + CS_COLS * RR_LDM;
@@ -362,7 +484,8 @@ __global__ void __launch_bounds__(RR_THREADS, 1) k_jacobi_rr(const JacobiTask<fl
   cs_dims(tk, nr, nc, k1, k2);
   const int tid = threadIdx.x, warp = tid >> 5, ln = tid & 31;
 
-  cs_load_core<RR_THREADS, RR_LDM>(tk, Mw, me, nr, nc, k1);
+  const bool pre = tk.load == 1 && pre_qr != 0;  // merge core: QR of E^T first
+  cs_load_core<RR_THREADS, RR_LDM>(tk, Mw, me, nr, nc, k1, pre);
   if (tid < 2) vote[tid] = 0;
   // every CTA of the cluster has started before any peer store
   cl_sync();
@@ -377,6 +500,74 @@ __global__ void __launch_bounds__(RR_THREADS, 1) k_jacobi_rr(const JacobiTask<fl
   rr_load<0>(x, Mw + cA * 8 * RR_LDM, nd, ln);
   rr_load<8>(x, Mw + cB * 8 * RR_LDM, nd, ln);
   __syncwarp();
+  if (pre) {
+    // ---- QR of E^T: panel P = global block P (CTA P / 16, block P % 16,
+    // held by warp (P % 16) % 8); panels 0..15 are applied in both CTAs
+    // (cluster barrier, reflectors copied to the peer's staging area),
+    // panels 16..31 only in CTA 1.  The staging area holds the reflectors
+    // (two buffers) until the first exchange of the sweeps.
+    constexpr int VSZ = 8 * 256 + 8;
+#pragma unroll 1
+    for (int P = 0; P < 32; ++P) {
+      if (me == 0 && P >= 16) break;  // CTA 0 holds no column after panel 15
+      float* vs = Stage + (P & 1) * VSZ;
+      float* taus = vs + 8 * 256;
+      if (me == (P >> 4) && warp == (P & 7)) {
+        if ((P & 15) < 8)
+          rr_panel<0>(x, P, vs, taus, ln);
+        else
+          rr_panel<8>(x, P, vs, taus, ln);
+        if (P < 16) {  // the peer's copy of the reflectors
+          __syncwarp();
+          const float4* src = reinterpret_cast<const float4*>(vs);
+          const uint32_t dst = cl_addr(vs, peer);
+          for (int e = ln; e < VSZ / 4; e += 32) cl_st4(dst + 16u * (uint32_t)e, src[e]);
+        }
+      }
+      if (P < 16)
+        cl_sync();
+      else
+        __syncthreads();
+      const int gA = me * 16 + cA, gB = me * 16 + cB;  // global panels held
+      if (gA > P) rr_apply_panel<0>(x, vs, taus, ln);
+      if (gB > P) rr_apply_panel<8>(x, vs, taus, ln);
+    }
+    // ---- R_e^T: slot s of CTA me becomes row s of R_e (R_e upper triangular:
+    // CTA 1's rows have entries in its own columns only; CTA 0's rows also
+    // in CTA 1's, whose top 128 rows are sent over)
+    rr_store<0, false>(x, Mw + cA * 8 * RR_LDM, peer, nd, ln);
+    rr_store<8, false>(x, Mw + cB * 8 * RR_LDM, peer, nd, ln);
+    cl_sync();  // both CTAs' columns stored, CTA 0 done with its staging area
+    if (me == 1) {
+      const uint32_t dst = cl_addr(Stage, peer);
+      for (int e = tid; e < 128 * 32; e += RR_THREADS) {  // [column c][row r < 128], compact rows of 128
+        const int c = e >> 5, r4 = (e & 31) * 4;
+        cl_st4(dst + 4u * (uint32_t)(c * 128 + r4), *reinterpret_cast<const float4*>(Mw + c * RR_LDM + r4));
+      }
+    }
+    cl_sync();
+    const int off = me == 0 ? 0 : 128;  // the diagonal 128 x 128 block of R_e held here
+    for (int e = tid; e < 128 * 128; e += RR_THREADS) {
+      const int c = e >> 7, r = e & 127;
+      if (c < r) {
+        const float a = Mw[c * RR_LDM + off + r], b = Mw[r * RR_LDM + off + c];
+        Mw[c * RR_LDM + off + r] = b;
+        Mw[r * RR_LDM + off + c] = a;
+      }
+    }
+    if (me == 0) {  // rows 128..255 of slot i: R_e[i][128 + c] from CTA 1
+      for (int e = tid; e < 128 * 128; e += RR_THREADS) {
+        const int i = e >> 7, c = e & 127;
+        Mw[i * RR_LDM + 128 + c] = Stage[c * 128 + i];
+      }
+    } else {  // rows 0..127 of CTA 1's slots: R_e[128 + i][c < 128] = 0
+      for (int e = tid; e < 128 * 128; e += RR_THREADS) Mw[(e >> 7) * RR_LDM + (e & 127)] = 0.f;
+    }
+    __syncthreads();
+    rr_load<0>(x, Mw + cA * 8 * RR_LDM, nd, ln);
+    rr_load<8>(x, Mw + cB * 8 * RR_LDM, nd, ln);
+    __syncwarp();
+  }
   bool converged = (nc <= 1);
   int sweep = 0;
   for (; sweep < tp.max_sweeps && !converged; ++sweep) {
@@ -432,6 +623,14 @@ __global__ void __launch_bounds__(RR_THREADS, 1) k_jacobi_rr(const JacobiTask<fl
   cs_finish<RR_THREADS, RR_LDM>(tk, Mw, me, nr, nc, k1, k2, tp, st, sig_s, perm, inv_s, &rank_s);
 }
 
+bool merge_qr_enabled() {  // HSVD_MERGE_QR=0: merge cores without the QR of E^T
+  static bool on = [] {
+    const char* e = std::getenv("HSVD_MERGE_QR");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 bool reg_enabled() {
   static bool on = [] {
     const char* e = std::getenv("HSVD_JACOBI_REG");
@@ -477,7 +676,7 @@ cudaError_t launch_jacobi_reg(const JacobiTask<float>* tasks, int ntasks, int nr
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_rr, tasks, tp, st);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_rr, tasks, tp, st, merge_qr_enabled() ? 1 : 0);
   if (e == cudaSuccess) *done = true;
   return e;
 }
