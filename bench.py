@@ -58,9 +58,9 @@ ORACLE_SIZE = 8192          # the recipe at this size is compared with the oracl
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 # DRAM bytes per unit of work of the dominant kernels, from ncu captures of
 # the current kernels (dram__bytes_read.sum + dram__bytes_write.sum): the
-# core SVDs per core (two launches of k_jacobi_rr at 8192^2: 23.50 MB over
+# core SVDs per core (two launches of k_jacobi_rr at 8192^2: 23.55 MB over
 # 96 cores of 256 x 256); absent where no capture of the current kernel exists
-TRAFFIC_PER_UNIT = {"jacobi": (17010176 + 15872 + 6474496 + 0) / 96}
+TRAFFIC_PER_UNIT = {"jacobi": (16979456 + 14592 + 6555392 + 0) / 96}
 
 
 def spectrum():
