@@ -1057,8 +1057,9 @@ struct Builder {
           }
           c.ldr = w.kl;
         }
-        ch.push_back(c);
         T* out = last ? w.Q : w.tmp;
+        if (!out) c.Rinv = nullptr;  // only R is wanted (no product follows): no inverse
+        ch.push_back(c);
         if (out) {
           Split3Task r;
           std::memset(&r, 0, sizeof(r));
@@ -1153,8 +1154,9 @@ struct Builder {
           }
           c.ldr = w.kl;
         }
-        ch.push_back(c);
         T* out = last ? w.Q : w.tmp;
+        if (!out) c.Rinv = nullptr;  // only R is wanted (no product follows): no inverse
+        ch.push_back(c);
         if (out) {
           mult.push_back(nn(in, ldin, w.h, w.k, w.Rinv, w.kl, w.k, out, w.kl));
           mult.back().btri = 1;  // R^{-1} is upper triangular
