@@ -164,10 +164,11 @@ template <class TA>
 cudaError_t launch_gemm_tn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);
 // 128 x 128 tiles for large FP32 products (items address 128 x 128 tiles; no
-// split-K, second A segment or beta term).
+// split-K; the second A segment of NN products and the beta term as in k_gemm2).
 constexpr int GEMM_WIDE_TILE = 128;
+// general: some task has a second A segment or a beta term (NN only).
 cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
-                             bool is_tn, const MatRef* mats, cudaStream_t s);
+                             bool is_tn, bool general, const MatRef* mats, cudaStream_t s);
 template <class TA>
 cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);

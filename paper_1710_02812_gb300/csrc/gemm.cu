@@ -600,22 +600,24 @@ __global__ void __launch_bounds__(128) k_gemm_nn_skinny(const GemmTask<TA, float
 // outputs (rows 8 ty .. 8 ty + 7, columns 4 tx .. 4 tx + 3 and 64 + 4 tx ..),
 // four 16-byte shared loads per 64 FMAs instead of three per 32; BK = 16 with
 // the next K tile loaded into registers while the current one is used.  No
-// split-K, no second A segment and no beta term (the caller only routes
-// products without them here); C = alpha A B or alpha A^T B.
+// split-K; C = alpha [A | A2] B + beta C0 (NN) or alpha A^T B (TN).
 constexpr int BM3 = 128, BN3 = 128, BK3 = 16;
 
-template <bool IS_TN>
+// GEN: some task of the launch has a second A segment or a beta term (the
+// plain form keeps the loads and the epilogue without them).
+template <bool IS_TN, bool GEN>
 __global__ void __launch_bounds__(256, 2) k_gemm3(const GemmTask<float, float, float>* __restrict__ tasks,
                                                const GemmItem* __restrict__ items, const MatRef* __restrict__ mats) {
   __shared__ __align__(16) float As[2][BK3][BM3 + 4];
   __shared__ __align__(16) float Bs[2][BK3][BN3 + 4];
   const GemmItem it = items[blockIdx.x];
   const GemmTask<float, float, float>& tk = tasks[it.task];
-  const int M = eff(tk.M), N = eff(tk.N), K = eff(tk.K);
+  const int M = eff(tk.M), N = eff(tk.N), K1 = eff(tk.K);
+  const int K2 = (GEN && !IS_TN && tk.A2) ? eff(tk.K2) : 0;  // NN: C = [A | A2] B
   const int m0 = it.mt * BM3, n0 = it.nt * BN3;
   if (m0 >= M || n0 >= N) return;
-  int ke = K;
-  if (!IS_TN && tk.btri) ke = min(ke, n0 + BN3);  // B upper triangular
+  int ke = K1 + K2;
+  if (!IS_TN && tk.btri && K2 == 0) ke = min(ke, n0 + BN3);  // B upper triangular
   const float* A = tk.A;
   int64_t lda = tk.lda;
   if (tk.mat >= 0) {
@@ -623,11 +625,13 @@ __global__ void __launch_bounds__(256, 2) k_gemm3(const GemmTask<float, float, f
     A = static_cast<const float*>(mr.ptr) + tk.r0 * mr.ld + tk.c0;
     lda = mr.ld;
   }
+  const float* A2 = tk.A2;
+  const int64_t lda2 = tk.lda2;
   const float* B = tk.B;
   const int64_t ldb = tk.ldb;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
-  const bool avec = aligned16(A, lda);
+  const bool avec = aligned16(A, lda) && (!GEN || K2 == 0 || aligned16(A2, lda2));
   const bool bvec = aligned16(B, ldb);
 
   float ra[8], rb[8];
@@ -635,11 +639,19 @@ __global__ void __launch_bounds__(256, 2) k_gemm3(const GemmTask<float, float, f
     if (!IS_TN) {  // A tile: 128 rows x 16 k, thread -> row tid >> 1, k (tid & 1) * 8
       const int r = tid >> 1, kk = (tid & 1) * 8;
       const int gm = m0 + r, gk = k0 + kk;
-      if (avec && gm < M && gk + 8 <= ke) {
-        load8(A + (int64_t)gm * lda + gk, ra);
+      // vector path: 8 elements inside one segment, 16-byte aligned in it
+      if (avec && gm < M && gk + 8 <= ke && (!GEN || gk + 8 <= K1 || (gk >= K1 && ((gk - K1) & 3) == 0))) {
+        if (!GEN || gk < K1)
+          load8(A + (int64_t)gm * lda + gk, ra);
+        else
+          load8(A2 + (int64_t)gm * lda2 + (gk - K1), ra);
       } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ra[i] = (gm < M && gk + i < ke) ? A[(int64_t)gm * lda + gk + i] : 0.f;
+        for (int i = 0; i < 8; ++i) {
+          const int g = gk + i;
+          ra[i] = (gm < M && g < ke) ? ((!GEN || g < K1) ? A[(int64_t)gm * lda + g] : A2[(int64_t)gm * lda2 + (g - K1)])
+                                     : 0.f;
+        }
       }
     } else {  // A tile: 16 k x 128 m, thread -> k tid >> 4, m (tid & 15) * 8
       const int kk = tid >> 4, mm = (tid & 15) * 8;
@@ -710,22 +722,28 @@ __global__ void __launch_bounds__(256, 2) k_gemm3(const GemmTask<float, float, f
     buf ^= 1;
   }
 
-  const float alpha = tk.alpha;
+  const float alpha = tk.alpha, beta = tk.beta;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int gm = m0 + ty * 8 + i;
     if (gm >= M) continue;
     float* crow = tk.C + (int64_t)gm * tk.ldc;
+    const float* c0row = (GEN && !IS_TN && tk.C0) ? tk.C0 + (int64_t)gm * tk.ldc0 : nullptr;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int gn = n0 + h * 64 + tx * 4;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[j] = alpha * acc[i][4 * h + j];
+        if (c0row && gn + j < N) v[j] += beta * c0row[gn + j];
+      }
       if (gn + 4 <= N && ((reinterpret_cast<uintptr_t>(crow + gn) & 15) == 0)) {
-        *reinterpret_cast<float4*>(crow + gn) = make_float4(alpha * acc[i][4 * h], alpha * acc[i][4 * h + 1],
-                                                            alpha * acc[i][4 * h + 2], alpha * acc[i][4 * h + 3]);
+        *reinterpret_cast<float4*>(crow + gn) = make_float4(v[0], v[1], v[2], v[3]);
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (gn + j < N) crow[gn + j] = alpha * acc[i][4 * h + j];
+          if (gn + j < N) crow[gn + j] = v[j];
       }
     }
   }
@@ -767,12 +785,14 @@ cudaError_t launch_gemm_reduce(const GemmTask<TA, TB, TC>* tasks, const GemmItem
 }
 
 cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
-                             bool is_tn, const MatRef* mats, cudaStream_t s) {
+                             bool is_tn, bool general, const MatRef* mats, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   if (is_tn)
-    k_gemm3<true><<<nitems, 256, 0, s>>>(tasks, items, mats);
+    k_gemm3<true, false><<<nitems, 256, 0, s>>>(tasks, items, mats);
+  else if (general)
+    k_gemm3<false, true><<<nitems, 256, 0, s>>>(tasks, items, mats);
   else
-    k_gemm3<false><<<nitems, 256, 0, s>>>(tasks, items, mats);
+    k_gemm3<false, false><<<nitems, 256, 0, s>>>(tasks, items, mats);
   return cudaGetLastError();
 }
 

@@ -448,9 +448,9 @@ struct Builder {
     }
   }
 
-  // Large FP32 products (no second A segment, no beta term, at least 128
-  // output rows and columns, enough 128 x 128 tiles to fill the GPU twice)
-  // run on 128 x 128 tiles without split-K.  HSVD_NO_WIDE turns this off.
+  // Large FP32 products (at least 128 output rows and columns, K up to 8192,
+  // enough 128 x 128 tiles to fill the GPU twice) run on 128 x 128 tiles
+  // without split-K.  HSVD_NO_WIDE turns this off.
   template <class G>
   bool emit_gemm_wide(const std::string& name, std::vector<G>& tasks, bool is_tn) {
     using TAx = typename TaOf<G>::type;
@@ -462,8 +462,10 @@ struct Builder {
       constexpr int W = GEMM_WIDE_TILE;
       int64_t tiles = 0;
       int ncols = 0;
+      bool general = false;
       for (const auto& g : tasks) {
-        if (g.A2 || g.C0 || g.K.cap > 8192) return false;
+        general = general || g.A2 || g.C0;
+        if (g.K.cap + (g.A2 ? g.K2.cap : 0) > 8192 || (is_tn && (g.A2 || g.C0))) return false;
         if (g.M.cap < W || g.N.cap < W) return false;
         for (int mt = 0; mt < cdiv(g.M.cap, W); ++mt)
           for (int nt = 0; nt < cdiv(g.N.cap, W); ++nt) tiles += (g.sym && nt < mt) ? 0 : 1;
@@ -488,8 +490,8 @@ struct Builder {
       PlanImpl* p = &P;
       const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
       const int ni = (int)items.size();
-      P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn](cudaStream_t s) {
-                               return launch_gemm_wide(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn,
+      P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn, general](cudaStream_t s) {
+                               return launch_gemm_wide(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn, general,
                                                        p->d_mats, s);
                              }});
       tag(is_tn ? 2 : 1, (int)tasks.size(), gcols, gfl, gby);
