@@ -169,6 +169,14 @@ constexpr int GEMM_WIDE_TILE = 128;
 // general: some task has a second A segment or a beta term (NN only).
 cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
                              bool is_tn, bool general, const MatRef* mats, cudaStream_t s);
+// FP32-grade tensor-core products of FP32 operands (tc_f32.cu): the tasks of
+// the SIMT kernels on 128 x 128 output tiles (items (task, tile row, tile
+// column, K chunk)); split-K partials in k_gemm2's layout (mtiles of 128 rows,
+// ntiles of 64 columns), summed by launch_gemm_reduce.  A of every task is a
+// plain pointer (mat < 0); TN tasks have no second segment and no beta term.
+// err counts CTAs whose bounded waits ran out.
+cudaError_t launch_tcf(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems, bool is_tn,
+                       int* err, cudaStream_t s);
 template <class TA>
 cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);

@@ -500,9 +500,106 @@ struct Builder {
     }
   }
 
+  // FP32 products of the BF16-mixed path on the tensor cores (k_tcf: three
+  // BF16 planes per operand made in shared memory, FP32-grade results), on
+  // 128 x 128 output tiles.  TN products whose tiles are too few to fill the
+  // GPU split K into chunks (partials and their ordered reduction as for
+  // k_gemm2).  Narrow products stay on the skinny SIMT kernels; products
+  // with the input matrix as A (FP32 path only) never come here.
+  // HSVD_NO_TCF keeps every product on the SIMT kernels.
+  static bool tcf_disabled() {
+    static const bool off = std::getenv("HSVD_NO_TCF") != nullptr;
+    return off;
+  }
+  template <class G>
+  bool emit_gemm_tcf(const std::string& name, std::vector<G>& tasks, bool is_tn) {
+    using TAx = typename TaOf<G>::type;
+    if constexpr (!std::is_same<T, float>::value || !std::is_same<TAx, float>::value) {
+      return false;
+    } else {
+      if (!P.use_tc || tcf_disabled()) return false;
+      constexpr int W = 128;
+      int sk = 1, kmax = 0;
+      int64_t tiles = 0;
+      for (const auto& g : tasks) {
+        if (g.mat >= 0 || (is_tn && (g.A2 || g.C0))) return false;
+        const int kin = g.K.cap + (g.A2 ? g.K2.cap : 0);
+        sk = std::max(sk, std::max(is_tn ? g.M.cap : kin, g.N.cap));
+        kmax = std::max(kmax, kin);
+        if (g.M.cap <= 0 || g.N.cap <= 0) continue;
+        for (int mt = 0; mt < cdiv(g.M.cap, W); ++mt)
+          for (int nt = 0; nt < cdiv(g.N.cap, W); ++nt) tiles += (g.sym && nt < mt) ? 0 : 1;
+      }
+      if (sk <= GEMM_SKINNY || tiles == 0) return false;
+      // K chunks per TN task: the count that minimises the launch's span in
+      // waves of one CTA per SM (chunks of at least 512 rows)
+      int split = 1;
+      if (is_tn) {
+        const int64_t nsm = num_sms();
+        double best = 1e300;
+        for (int sp = 1; sp <= std::min(64, std::max(1, kmax / 512)); ++sp) {
+          const double span = (double)((tiles * sp + nsm - 1) / nsm) / sp;
+          if (span < best - 1e-9) {
+            best = span;
+            split = sp;
+          }
+        }
+      }
+      std::vector<GemmItem> items, red;
+      for (size_t t = 0; t < tasks.size(); ++t) {
+        G& g = tasks[t];
+        g.mtiles = cdiv(g.M.cap, W);           // partial tiles: 128 rows
+        g.ntiles = cdiv(g.N.cap, GEMM_TILE_N); // x 64 columns (k_gemm2's layout)
+        g.nkc = 1;
+        g.kchunk = 0;
+        g.partial = nullptr;
+        if (g.M.cap <= 0 || g.N.cap <= 0) continue;
+        const int ktot = g.K.cap;
+        if (split > 1 && ktot > 512) {
+          const int chunk = (int)(((ktot + split - 1) / split + 63) / 64 * 64);
+          if (ktot > chunk) {
+            g.kchunk = chunk;
+            g.nkc = cdiv(ktot, chunk);
+            g.partial = alloc<T>((size_t)g.nkc * g.mtiles * g.ntiles * W * GEMM_TILE_N);
+            for (int mt = 0; mt < g.mtiles; ++mt)
+              for (int nt = 0; nt < g.ntiles; ++nt)
+                if (!below_diag(g, mt, nt))
+                  for (int q = 0; q < GEMM_REDUCE_PARTS; ++q) red.push_back(GemmItem{(int)t, mt, nt, q});
+          }
+        }
+        for (int kc = 0; kc < g.nkc; ++kc)
+          for (int mt = 0; mt < cdiv(g.M.cap, W); ++mt)
+            for (int nt = 0; nt < cdiv(g.N.cap, W); ++nt)
+              if (!(g.sym && nt < mt)) items.push_back(GemmItem{(int)t, mt, nt, kc});
+      }
+      double gfl, gby;
+      int gcols;
+      gemm_work(tasks, is_tn, gfl, gby, gcols);
+      PlanImpl* p = &P;
+      const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
+      const int ni = (int)items.size();
+      P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn](cudaStream_t s) {
+                               return launch_tcf(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn,
+                                                 &p->d_status->tc_timeouts, s);
+                             }});
+      tag(8, (int)tasks.size(), gcols, gfl, gby);
+      if (!red.empty()) {
+        const size_t br = P.add_blob(red);
+        const int nr = (int)red.size();
+        P.steps.push_back(Step{name + ".reduce", [p, bt, br, nr](cudaStream_t s) {
+                                 return launch_gemm_reduce<float, float, float>(p->table<G>(bt),
+                                                                                p->table<GemmItem>(br), nr, s);
+                               }});
+        tag(3, (int)tasks.size(), gcols, 0, 0);
+      }
+      return true;
+    }
+  }
+
   template <class G>
   void emit_gemm(const std::string& name, std::vector<G> tasks, bool is_tn) {
     if (tasks.empty()) return;
+    if (emit_gemm_tcf(name, tasks, is_tn)) return;
     if (emit_gemm_wide(name, tasks, is_tn)) return;
     std::vector<GemmItem> items, red;
     finish_items(tasks, is_tn, items, red);
@@ -921,8 +1018,14 @@ struct Builder {
     static const bool off = std::getenv("HSVD_NO_TC3") != nullptr;
     return off;
   }
+  // HSVD_ORTH_TCF: the block stage's CholeskyQR products on k_tcf (FP32 operands
+  // split in shared memory) instead of the plane arenas and k_tc_gemm3
+  static bool orth_tcf() {
+    static const bool on = std::getenv("HSVD_ORTH_TCF") != nullptr;
+    return on;
+  }
   bool tc3_eligible(const std::vector<OrthW>& ws, int kcapl) const {
-    if (!std::is_same<T, float>::value || !P.use_tc || tc3_disabled()) return false;
+    if (!std::is_same<T, float>::value || !P.use_tc || tc3_disabled() || orth_tcf()) return false;
     if (kcapl != 128 && kcapl != 256) return false;
     for (const auto& w : ws)
       if (w.k.dyn || w.k.cap != kcapl || w.kl != kcapl || w.h < 1 || w.h > 1024) return false;
