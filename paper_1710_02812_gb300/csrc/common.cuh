@@ -177,6 +177,12 @@ cudaError_t launch_gemm_wide(const GemmTask<float, float, float>* tasks, const G
 // err counts CTAs whose bounded waits ran out.
 cudaError_t launch_tcf(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems, bool is_tn,
                        int* err, cudaStream_t s);
+// The TMA-fed form: the same tasks and items, FP32 tiles loaded by TMA through
+// three tensor maps per task (tcf_task_maps: A, B, A2; false when a base or
+// stride breaks TMA's rules, and the launch then takes launch_tcf).
+cudaError_t launch_tcf_tma(const GemmTask<float, float, float>* tasks, const GemmItem* items, int nitems,
+                           const void* maps, bool is_tn, int* err, cudaStream_t s);
+bool tcf_task_maps(const GemmTask<float, float, float>& t, bool is_tn, void* out3);
 template <class TA>
 cudaError_t launch_gemm_nn_skinny(const GemmTask<TA, float, float>* tasks, const GemmItem* items, int nitems,
                                   int sk, const MatRef* mats, cudaStream_t s);
@@ -279,6 +285,8 @@ struct TcRedTask {
   int64_t ldd;
 };
 bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+bool make_tmap_f32(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                   int box_rows, bool swz128);
 cudaError_t launch_tc_reduce(const TcRedTask* tasks, const int2* items, int nitems, cudaStream_t s);
 bool tc_available();  // the CUDA driver's tensor-map encoder could be resolved
 

@@ -511,6 +511,11 @@ struct Builder {
     static const bool off = std::getenv("HSVD_NO_TCF") != nullptr;
     return off;
   }
+  // HSVD_TCF_NO_TMA: the converter warps load the FP32 tiles themselves (k_tcf)
+  static bool tcf_tma_disabled() {
+    static const bool off = std::getenv("HSVD_TCF_NO_TMA") != nullptr;
+    return off;
+  }
   template <class G>
   bool emit_gemm_tcf(const std::string& name, std::vector<G>& tasks, bool is_tn) {
     using TAx = typename TaOf<G>::type;
@@ -572,16 +577,37 @@ struct Builder {
             for (int nt = 0; nt < cdiv(g.N.cap, W); ++nt)
               if (!(g.sym && nt < mt)) items.push_back(GemmItem{(int)t, mt, nt, kc});
       }
+      // FP32 tiles by TMA (k_tcf2) for TN products and products with a beta
+      // term, when every task's bases and strides allow tensor maps; plain NN
+      // products keep the converter warps' own loads (k_tcf), which measured
+      // faster for them (the TMA form's 32-deep K tiles double the stage
+      // hand-offs of their 128-deep K loops)
+      struct alignas(64) Map128 {
+        unsigned char b[128];
+      };
+      bool want_tma = is_tn;
+      for (const auto& g : tasks) want_tma = want_tma || g.C0;
+      std::vector<Map128> maps(3 * tasks.size());
+      bool tma = want_tma && !tcf_tma_disabled();
+      for (size_t t = 0; t < tasks.size() && tma; ++t) tma = tcf_task_maps(tasks[t], is_tn, &maps[3 * t]);
       double gfl, gby;
       int gcols;
       gemm_work(tasks, is_tn, gfl, gby, gcols);
       PlanImpl* p = &P;
       const size_t bt = P.add_blob(tasks), bi = P.add_blob(items);
       const int ni = (int)items.size();
-      P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn](cudaStream_t s) {
-                               return launch_tcf(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn,
-                                                 &p->d_status->tc_timeouts, s);
-                             }});
+      if (tma) {
+        const size_t bm = P.add_blob(maps);
+        P.steps.push_back(Step{name, [p, bt, bi, bm, ni, is_tn](cudaStream_t s) {
+                                 return launch_tcf_tma(p->table<G>(bt), p->table<GemmItem>(bi), ni,
+                                                       p->table<Map128>(bm), is_tn, &p->d_status->tc_timeouts, s);
+                               }});
+      } else {
+        P.steps.push_back(Step{name, [p, bt, bi, ni, is_tn](cudaStream_t s) {
+                                 return launch_tcf(p->table<G>(bt), p->table<GemmItem>(bi), ni, is_tn,
+                                                   &p->d_status->tc_timeouts, s);
+                               }});
+      }
       tag(8, (int)tasks.size(), gcols, gfl, gby);
       if (!red.empty()) {
         const size_t br = P.add_blob(red);

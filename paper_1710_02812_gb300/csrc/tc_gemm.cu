@@ -513,6 +513,28 @@ bool make_tmap_bf16(void* out128, const void* base, int64_t rows, int64_t cols, 
   return r == CUDA_SUCCESS;
 }
 
+// Tensor map of a row-major FP32 matrix (rows x cols, leading dimension ld
+// elements) read in boxes of box_cols x box_rows: with swz128 the 128-byte
+// swizzle (box_cols = 32, one 128-byte row), else unswizzled (box_cols up to
+// 256).  The base must be 16-byte aligned and ld a multiple of 4; out-of-range
+// parts of a box read zeros.
+bool make_tmap_f32(void* out128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                   int box_rows, bool swz128) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || box_rows < 1 || box_rows > 256 || box_cols < 4 || box_cols > 256 || (box_cols & 3)) return false;
+  if (swz128 && box_cols != 32) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16 || rows < 1 || cols < 1) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(out128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swz128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool tc_available() { return encode_fn() != nullptr; }
 
 size_t tc_smem_bytes(int stages, int bmax) {

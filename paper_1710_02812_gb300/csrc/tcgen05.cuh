@@ -74,6 +74,30 @@ static __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for K-major tiles of 64-byte rows (32 BF16) in the 64-byte swizzle
+// (16-byte chunk c of row r at chunk c ^ ((r >> 1) & 3)): stride byte offset
+// 512 between groups of 8 rows, layout type 4.  Tiles are 512-byte aligned.
+static __device__ __forceinline__ uint64_t desc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(16 >> 4) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
+
+// A TMA tile load into a shared-memory address (32-bit shared window) with
+// completion on an mbarrier given by its shared address.
+static __device__ __forceinline__ void tma_load_2d_s(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                                     int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
 // Instruction descriptor of kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits
 // 7-9 = 1), B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 (bits 17-22), M >> 4 (bits 24-28).
