@@ -97,25 +97,59 @@ __global__ void __launch_bounds__(256) k_convert_input4(const float* __restrict_
 
 // One CTA per (task, 32-row tile of B^T, 32-column tile): reads B[k][n] tiles
 // coalesced along n and writes B^T[n][k] coalesced along k.
+// Items (task, 64-row tile of the output, 64-column tile): a 64 x 64 tile of
+// B (K rows x N columns) read with float4 loads where the strides allow,
+// split into hi and lo, staged transposed in shared memory (rows of 65
+// elements: the 16 column quads of a warp's stores fall in 16 banks), and
+// written as packed 8-byte groups of four BF16 along the output rows.
 __global__ void __launch_bounds__(256) k_make_bt(const BtTask* __restrict__ tasks, const int3* __restrict__ items) {
-  __shared__ float tile[32][33];
+  __shared__ __nv_bfloat16 sh[2][64][65];  // [hi / lo][output row (source column)][output column (source row)]
   const int3 it = items[blockIdx.x];
   const BtTask tk = tasks[it.x];
-  const int n0 = it.y * 32, k0 = it.z * 32;
+  const int n0 = it.y * 64, k0 = it.z * 64;
   const int N = eff(tk.N);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int i = ty; i < 32; i += 8) {
-    const int k = k0 + i, n = n0 + tx;
-    tile[i][tx] = (k < tk.K && n < N) ? tk.B[static_cast<int64_t>(k) * tk.ldb + n] : 0.f;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 column quads x 16 rows
+  const bool vin = (tk.ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(tk.B) & 15) == 0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int kr = ty + 16 * q, k = k0 + kr, nc = 4 * tx, n = n0 + nc;
+    float v[4];
+    if (vin && k < tk.K && n + 3 < N) {
+      const float4 f = *reinterpret_cast<const float4*>(tk.B + static_cast<int64_t>(k) * tk.ldb + n);
+      v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (k < tk.K && n + e < N) ? tk.B[static_cast<int64_t>(k) * tk.ldb + n + e] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
+      sh[0][nc + e][kr] = hi;
+      sh[1][nc + e][kr] = __float2bfloat16_rn(v[e] - __bfloat162float(hi));
+    }
   }
   __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int n = n0 + i, k = k0 + tx;
+  const bool vo = (tk.kpad % 4 == 0) && ((reinterpret_cast<uintptr_t>(tk.hi) & 7) == 0) &&
+                  (!tk.lo || (reinterpret_cast<uintptr_t>(tk.lo) & 7) == 0);
+  const int np = tk.lo ? 2 : 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int oc = ty + 16 * q, n = n0 + oc, k = k0 + 4 * tx;
     if (n >= tk.bmax || k >= tk.kpad) continue;
-    const float v = tile[tx][i];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    tk.hi[static_cast<int64_t>(n) * tk.kpad + k] = hi;
-    if (tk.lo) tk.lo[static_cast<int64_t>(n) * tk.kpad + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    for (int p = 0; p < np; ++p) {
+      __nv_bfloat16* o = (p == 0 ? tk.hi : tk.lo) + static_cast<int64_t>(n) * tk.kpad + k;
+      const __nv_bfloat16* sv = &sh[p][oc][4 * tx];
+      if (vo && k + 3 < tk.kpad) {
+        uint2 w;
+        w.x = static_cast<uint32_t>(__bfloat16_as_ushort(sv[0])) | (static_cast<uint32_t>(__bfloat16_as_ushort(sv[1])) << 16);
+        w.y = static_cast<uint32_t>(__bfloat16_as_ushort(sv[2])) | (static_cast<uint32_t>(__bfloat16_as_ushort(sv[3])) << 16);
+        *reinterpret_cast<uint2*>(o) = w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (k + e < tk.kpad) o[e] = sv[e];
+      }
+    }
   }
 }
 

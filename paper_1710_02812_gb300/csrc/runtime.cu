@@ -840,8 +840,8 @@ struct Builder {
       b.kpad = kpad;
       b.bmax = bmax;
       bt.push_back(b);
-      for (int nt = 0; nt < bmax / 32 + (bmax % 32 ? 1 : 0); ++nt)
-        for (int kt = 0; kt < kpad / 32; ++kt) bti.push_back(make_int3((int)q, nt, kt));
+      for (int nt = 0; nt < (bmax + 63) / 64; ++nt)  // 64 x 64 tiles of the transposed output
+        for (int kt = 0; kt < (kpad + 63) / 64; ++kt) bti.push_back(make_int3((int)q, nt, kt));
     }
     for (size_t t = 0; t < ops.size(); ++t) {
       const InputOp& o = ops[t];
