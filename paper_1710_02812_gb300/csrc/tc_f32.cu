@@ -109,6 +109,32 @@ __device__ __forceinline__ void split8(const float* v, uint4& h, uint4& m, uint4
   l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+// Bounded wait (~1 s) that also gives up as soon as another role of the CTA
+// has failed, so a CTA whose issuer stopped ends without each role's own
+// full limit.
+__device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, const int* failed) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*(volatile const int*)failed || clock64() - t0 > TC_WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
+// The MMA issuer's wait for a stage; the very first one of the CTA gives up
+// after first_wait cycles when first_wait > 0 (a test of the timeout path).
+__device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity, const int* failed, bool& first,
+                                           long long first_wait) {
+  if (first && first_wait > 0) {
+    first = false;
+    const long long t0 = clock64();
+    bool got = mbar_test(bar, parity);
+    while (!got && clock64() - t0 < first_wait) got = mbar_test(bar, parity);
+    return got;
+  }
+  first = false;
+  return wait_live(bar, parity, failed);
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, const uint4& v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
@@ -277,7 +303,7 @@ __device__ __forceinline__ void tf_epilogue(const G32* __restrict__ tasks, const
 template <bool IS_TN>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_tcf(const G32* __restrict__ tasks,
                                                      const GemmItem* __restrict__ items, int nitems,
-                                                     int* __restrict__ err) {
+                                                     int* __restrict__ err, long long first_wait) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[TF_STAGES];
   __shared__ __align__(8) uint64_t empty_bar[TF_STAGES];
@@ -384,7 +410,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tcf(const G32* __restrict__ t
               }
           }
         }
-        if (g >= TF_STAGES && !mbar_wait(&empty_bar[s], ((g / TF_STAGES) - 1) & 1)) {
+        if (g >= TF_STAGES && !wait_live(&empty_bar[s], ((g / TF_STAGES) - 1) & 1, &failed)) {
           fail();
           ok = false;
           break;
@@ -420,13 +446,14 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tcf(const G32* __restrict__ t
     // ---- MMA issuer: live item j into the accumulator pair (j & 1)
     if (lane == 0) {
       int g = 0, j = 0;
+      bool first = true;
       const uint32_t idesc = idesc_bf16_f32(TC_BM, TF_BN);
       for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x) {
         const GemmItem it = items[i];
         const TfView vw = tf_view<IS_TN, TC_BK>(tasks[it.task], it);
         if (!vw.live) continue;
         const int a = j & 1;
-        if (j >= 2 && !mbar_wait(&tempty_bar[a], ((j >> 1) - 1) & 1)) {
+        if (j >= 2 && !wait_live(&tempty_bar[a], ((j >> 1) - 1) & 1, &failed)) {
           fail();
           break;
         }
@@ -437,7 +464,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tcf(const G32* __restrict__ t
         bool ok = true;
         for (int kt = 0; kt < vw.nk; ++kt, ++g) {
           const int s = g % TF_STAGES;
-          if (!mbar_wait(&full_bar[s], (g / TF_STAGES) & 1)) {
+          if (!wait_stage(&full_bar[s], (g / TF_STAGES) & 1, &failed, first, first_wait)) {
             fail();
             ok = false;
             break;
@@ -518,7 +545,8 @@ __device__ __forceinline__ void mbar_arrive_s(uint64_t* bar) {
 template <bool IS_TN>
 __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ tasks,
                                                       const GemmItem* __restrict__ items, int nitems,
-                                                      const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+                                                      const CUtensorMap* __restrict__ maps, int* __restrict__ err,
+                                                      long long first_wait) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t ffull[T2_NFS];
   __shared__ __align__(8) uint64_t fempty[T2_NFS];
@@ -575,7 +603,7 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
         bool ok = true;
         for (int kt = 0; kt < vw.nk; ++kt, ++g) {
           const int f = g % T2_NFS;
-          if (g >= T2_NFS && !mbar_wait(&fempty[f], ((g / T2_NFS) - 1) & 1)) {
+          if (g >= T2_NFS && !wait_live(&fempty[f], ((g / T2_NFS) - 1) & 1, &failed)) {
             fail();
             ok = false;
             break;
@@ -631,7 +659,7 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
         const int f = g % T2_NFS, p = g % T2_NPS;
         const int k0 = vw.kb + kt * T2_BK;
         const int kv = vw.ke - k0;  // valid K columns of this tile (may be <= 0)
-        if (!mbar_wait(&ffull[f], (g / T2_NFS) & 1)) {
+        if (!wait_live(&ffull[f], (g / T2_NFS) & 1, &failed)) {
           fail();
           ok = false;
           break;
@@ -677,7 +705,7 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
         // the FP32 stage is free for the next TMA load once every warp has read it
         __syncwarp();
         if (lane == 0) mbar_arrive_s(&fempty[f]);
-        if (g >= T2_NPS && !mbar_wait(&pempty[p], ((g / T2_NPS) - 1) & 1)) {
+        if (g >= T2_NPS && !wait_live(&pempty[p], ((g / T2_NPS) - 1) & 1, &failed)) {
           fail();
           ok = false;
           break;
@@ -712,13 +740,14 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
     // ---- MMA issuer
     if (lane == 0) {
       int g = 0, j = 0;
+      bool first = true;
       const uint32_t idesc = idesc_bf16_f32(TC_BM, TF_BN);
       for (int i = blockIdx.x; i < nitems && !*(volatile int*)&failed; i += gridDim.x) {
         const GemmItem it = items[i];
         const TfView vw = tf_view<IS_TN, T2_BK>(tasks[it.task], it);
         if (!vw.live) continue;
         const int a = j & 1;
-        if (j >= 2 && !mbar_wait(&tempty_bar[a], ((j >> 1) - 1) & 1)) {
+        if (j >= 2 && !wait_live(&tempty_bar[a], ((j >> 1) - 1) & 1, &failed)) {
           fail();
           break;
         }
@@ -729,7 +758,7 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
         bool ok = true;
         for (int kt = 0; kt < vw.nk; ++kt, ++g) {
           const int p = g % T2_NPS;
-          if (!mbar_wait(&pfull[p], (g / T2_NPS) & 1)) {
+          if (!wait_stage(&pfull[p], (g / T2_NPS) & 1, &failed, first, first_wait)) {
             fail();
             ok = false;
             break;
@@ -770,6 +799,16 @@ __global__ void __launch_bounds__(T2_THREADS, 1) k_tcf2(const G32* __restrict__ 
 }
 }  // namespace
 
+// test only: a short first wait of the MMA issuer (cycles, 0 = off) that
+// exercises the timeout path, as for k_tc_gemm
+long long tcf_first_wait() {
+  static const long long v = [] {
+    const char* e = std::getenv("HSVD_TC_FIRST_WAIT_CYCLES");
+    return e ? std::atoll(e) : 0LL;
+  }();
+  return v;
+}
+
 // the stage ring, the epilogue's four 32 x 36 FP32 staging blocks, alignment slack
 size_t tcf_smem_bytes() { return static_cast<size_t>(TF_STAGES) * TF_STAGE + 4 * 32 * 36 * 4 + 1024; }
 
@@ -791,11 +830,11 @@ cudaError_t launch_tcf(const GemmTask<float, float, float>* tasks, const GemmIte
   if (is_tn) {
     e = cudaFuncSetAttribute(k_tcf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_tcf<true><<<grid, TF_THREADS, bytes, s>>>(tasks, items, nitems, err);
+    k_tcf<true><<<grid, TF_THREADS, bytes, s>>>(tasks, items, nitems, err, tcf_first_wait());
   } else {
     e = cudaFuncSetAttribute(k_tcf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_tcf<false><<<grid, TF_THREADS, bytes, s>>>(tasks, items, nitems, err);
+    k_tcf<false><<<grid, TF_THREADS, bytes, s>>>(tasks, items, nitems, err, tcf_first_wait());
   }
   return cudaGetLastError();
 }
@@ -821,11 +860,11 @@ cudaError_t launch_tcf_tma(const GemmTask<float, float, float>* tasks, const Gem
   if (is_tn) {
     e = cudaFuncSetAttribute(k_tcf2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_tcf2<true><<<grid, T2_THREADS, bytes, s>>>(tasks, items, nitems, m, err);
+    k_tcf2<true><<<grid, T2_THREADS, bytes, s>>>(tasks, items, nitems, m, err, tcf_first_wait());
   } else {
     e = cudaFuncSetAttribute(k_tcf2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_tcf2<false><<<grid, T2_THREADS, bytes, s>>>(tasks, items, nitems, m, err);
+    k_tcf2<false><<<grid, T2_THREADS, bytes, s>>>(tasks, items, nitems, m, err, tcf_first_wait());
   }
   return cudaGetLastError();
 }

@@ -675,14 +675,17 @@ def test_autotune_picks_measured_variants_and_keeps_parity():
     assert st["not_converged"] == 0 and st["nonfinite"] == 0 and st["tensor_timeouts"] == 0
 
 
-def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(tmp_path):
-    """The bounded waits of the tensor-core kernel: a test-only limit
+@pytest.mark.parametrize("k", [16, 48])
+def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(tmp_path, k):
+    """The bounded waits of the tensor-core kernels: a test-only limit
     (HSVD_TC_FIRST_WAIT_CYCLES, read once per process) makes the MMA issuer's
     first wait give up before its tiles land; the kernel sets the error word,
-    waits (with the full limit) for its own copies and MMAs, frees its tensor
-    memory and returns.  Run in a child process: the run reports
-    tensor_timeouts > 0 and the CUDA context stays usable (a plain FP32 plan
-    afterwards matches the oracle)."""
+    its other roles give up their waits, it waits for its own copies and
+    MMAs, frees its tensor memory and returns.  k = 16: the input products
+    (k_tc_gemm); k = 48: also the FP32-grade factor products (k_tcf, k_tcf2),
+    wider than the skinny kernels' 32.  Run in a child process: the run
+    reports tensor_timeouts > 0 and the CUDA context stays usable (a plain
+    FP32 plan afterwards matches the oracle)."""
     import subprocess
     import sys
     code = f"""
@@ -692,7 +695,7 @@ from paper_1710_02812_gb300 import hsvd, workloads as W
 import oracle
 x = W.exp_decay(512, 512, r=100, noise=1e-5, tag=81, dtype=np.float32)
 xd = torch.from_numpy(x).cuda()
-p = hsvd.Plan(512, 512, 256, 256, "fixed_k", 16, prec="bf16_mixed", power_iters=1)
+p = hsvd.Plan(512, 512, 256, 256, "fixed_k", {k}, prec="bf16_mixed", power_iters=1)
 p.run([xd])
 st = p.status()
 assert st["tensor_timeouts"] > 0, st
